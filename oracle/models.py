@@ -1,0 +1,100 @@
+"""Direct numpy restatements of the benchmark models (test infrastructure).
+
+These do not trace anything and share no code with the program generators:
+they restate each model from its definition, with derivatives derived by hand,
+so that a generated program can be checked against them through the oracle.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# cart-pole (frictionless cart, point-mass pole on a massless rod of length l,
+# theta = 0 hanging down); state [x, th, xd, thd], input f
+# ---------------------------------------------------------------------------
+def cartpole_f(q, f, m_c=1.0, m_p=0.1, l=0.5, g=9.81):
+    x, th, xd, thd = q
+    s, c = np.sin(th), np.cos(th)
+    D = m_c + m_p * s ** 2
+    xdd = (f + m_p * s * (l * thd ** 2 + g * c)) / D
+    thdd = (-f * c - m_p * l * thd ** 2 * c * s - (m_c + m_p) * g * s) / (l * D)
+    return np.array([xd, thd, xdd, thdd])
+
+
+def cartpole_jf(q, f, m_c=1.0, m_p=0.1, l=0.5, g=9.81):
+    """4x5 Jacobian of the continuous dynamics w.r.t. [x, th, xd, thd, f], by hand."""
+    _, th, _, w = q
+    s, c = math.sin(th), math.cos(th)
+    D = m_c + m_p * s * s
+    dD = 2 * m_p * s * c
+    Nx = f + m_p * s * l * w * w + m_p * g * s * c
+    dNx = m_p * c * l * w * w + m_p * g * (c * c - s * s)
+    Nt = -f * c - m_p * l * w * w * c * s - (m_c + m_p) * g * s
+    dNt = f * s - m_p * l * w * w * (c * c - s * s) - (m_c + m_p) * g * c
+    J = np.zeros((4, 5))
+    J[0, 2] = 1.0
+    J[1, 3] = 1.0
+    J[2, 1] = (dNx * D - Nx * dD) / D ** 2
+    J[2, 3] = 2 * m_p * s * l * w / D
+    J[2, 4] = 1.0 / D
+    J[3, 1] = (dNt * D - Nt * dD) / (l * D ** 2)
+    J[3, 3] = -2 * m_p * l * w * c * s / (l * D)
+    J[3, 4] = -c / (l * D)
+    return J
+
+
+def cartpole_rk4_with_jacobian(q, f, dt=0.01, **p):
+    """RK4 step and d q+ / d [q; f], the stage Jacobians chained by hand."""
+    q = np.asarray(q, dtype=np.float64)
+    E = np.hstack([np.eye(4), np.zeros((4, 1))])   # d q / d z
+    eu = np.array([[0, 0, 0, 0, 1.0]])              # d f / d z
+    k1 = cartpole_f(q, f, **p)
+    dk1 = cartpole_jf(q, f, **p) @ np.vstack([E, eu])
+    q2 = q + 0.5 * dt * k1
+    dq2 = E + 0.5 * dt * dk1
+    k2 = cartpole_f(q2, f, **p)
+    dk2 = cartpole_jf(q2, f, **p) @ np.vstack([dq2, eu])
+    q3 = q + 0.5 * dt * k2
+    dq3 = E + 0.5 * dt * dk2
+    k3 = cartpole_f(q3, f, **p)
+    dk3 = cartpole_jf(q3, f, **p) @ np.vstack([dq3, eu])
+    q4 = q + dt * k3
+    dq4 = E + dt * dk3
+    k4 = cartpole_f(q4, f, **p)
+    dk4 = cartpole_jf(q4, f, **p) @ np.vstack([dq4, eu])
+    qn = q + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    Jn = E + dt / 6.0 * (dk1 + 2 * dk2 + 2 * dk3 + dk4)
+    return qn, Jn
+
+
+def cartpole_linearization(m_c=1.0, m_p=0.1, l=0.5, g=9.81):
+    """A_c, B_c of the dynamics at the hanging equilibrium, in closed form."""
+    A = np.array([[0, 0, 1, 0], [0, 0, 0, 1],
+                  [0, m_p * g / m_c, 0, 0],
+                  [0, -(m_c + m_p) * g / (l * m_c), 0, 0]], dtype=np.float64)
+    B = np.array([[0], [0], [1 / m_c], [-1 / (l * m_c)]], dtype=np.float64)
+    return A, B
+
+
+def rk4_linear_maps(A, B, dt):
+    """RK4 on x' = A x + B u with u held: x+ = T4(A dt) x + S4 B u where
+    T4 = sum_{k<=4} (A dt)^k / k! and S4 = sum_{k=1..4} A^(k-1) dt^k / k!."""
+    n = A.shape[0]
+    T4 = np.zeros((n, n))
+    S4 = np.zeros((n, n))
+    P = np.eye(n)
+    for k in range(0, 5):
+        T4 += np.linalg.matrix_power(A * dt, k) / math.factorial(k)
+        if k >= 1:
+            S4 += np.linalg.matrix_power(A, k - 1) * dt ** k / math.factorial(k)
+    return T4, S4 @ B
+
+
+# ---------------------------------------------------------------------------
+# pendulum: th'' = -(g/l) sin th; energy E = om^2 / 2 - (g/l) cos th
+# ---------------------------------------------------------------------------
+def pendulum_energy(th, om, g_over_l=9.81):
+    return 0.5 * np.asarray(om) ** 2 - g_over_l * np.cos(th)

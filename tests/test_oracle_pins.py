@@ -1,0 +1,327 @@
+"""Pins of the oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle (or a generated program run through it) against
+something that is not the oracle: a closed form, an invariant, a hand-derived
+derivative, a high-precision evaluation, or a brute-force re-derivation.
+"""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+
+from oracle import MODE_F32, MODE_F64, Oracle, OracleError
+from oracle import models as M
+from oracle.mp_eval import mp_eval
+from paper_2408_09662_gb300 import inputs, programs
+from paper_2408_09662_gb300.ir import BINARY, Instr, Op, ProgramIR, Sparsity
+
+
+# ---------------------------------------------------------------------------
+# Listing 2 worked example
+# ---------------------------------------------------------------------------
+def test_listing2_golden_file_matches_listing():
+    """tests/golden/listing2.txt spells out the Listing 2 instruction stream."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "listing2.txt")
+    lines = [l.split("#")[0].split() for l in open(path) if l.split("#")[0].strip()]
+    ir = programs.listing2()
+    assert len(lines) == len(ir.instrs)
+    for toks, ins in zip(lines, ir.instrs):
+        assert Op[toks[0]] == ins.op
+        assert [int(t) for t in toks[1:]] == [ins.out, ins.a, ins.b][: len(toks) - 1]
+
+
+def test_listing2_closed_form():
+    """y = (sin x + x)^2, evaluated with the in-place slot reuse of Listing 2."""
+    x = np.linspace(-7.0, 7.0, 1001)[None, :]
+    y = Oracle(programs.listing2().to_bytes()).eval(x)
+    ref = (np.sin(x[0]) + x[0]) ** 2
+    np.testing.assert_allclose(y[0], ref, rtol=4e-16, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# single ops: op-code mapping and operand order against mpmath at 40 digits
+# ---------------------------------------------------------------------------
+_DOMAIN = {
+    Op.LOG: (0.1, 5.0), Op.SQRT: (0.0, 9.0), Op.ASIN: (-0.99, 0.99), Op.ACOS: (-0.99, 0.99),
+    Op.LOG1P: (-0.9, 4.0), Op.POW: (0.1, 3.0), Op.INV: (0.5, 3.0), Op.DIV: (-3.0, 3.0),
+    Op.TAN: (-1.4, 1.4), Op.FMOD: (-5.0, 5.0),
+}
+
+_MPF = {
+    Op.ADD: lambda a, b: a + b, Op.SUB: lambda a, b: a - b, Op.MUL: lambda a, b: a * b,
+    Op.DIV: lambda a, b: a / b, Op.NEG: lambda a, b: -a, Op.EXP: lambda a, b: mpmath.exp(a),
+    Op.LOG: lambda a, b: mpmath.log(a), Op.POW: lambda a, b: mpmath.power(a, b),
+    Op.SQ: lambda a, b: a * a, Op.SQRT: lambda a, b: mpmath.sqrt(a),
+    Op.SIN: lambda a, b: mpmath.sin(a), Op.COS: lambda a, b: mpmath.cos(a),
+    Op.TAN: lambda a, b: mpmath.tan(a), Op.ATAN: lambda a, b: mpmath.atan(a),
+    Op.ATAN2: lambda a, b: mpmath.atan2(a, b), Op.TANH: lambda a, b: mpmath.tanh(a),
+    Op.FABS: lambda a, b: abs(a), Op.FMIN: lambda a, b: min(a, b), Op.FMAX: lambda a, b: max(a, b),
+    Op.FMA_CONST: lambda a, b: mpmath.mpf(0.75) * a + b,
+    Op.IF_ELSE_ZERO: lambda a, b: b if a != 0 else 0,
+    Op.LT: lambda a, b: float(a < b), Op.LE: lambda a, b: float(a <= b),
+    Op.EQ: lambda a, b: float(a == b), Op.NE: lambda a, b: float(a != b),
+    Op.NOT: lambda a, b: float(a == 0), Op.AND: lambda a, b: float(a != 0 and b != 0),
+    Op.OR: lambda a, b: float(a != 0 or b != 0), Op.ASIN: lambda a, b: mpmath.asin(a),
+    Op.ACOS: lambda a, b: mpmath.acos(a), Op.SINH: lambda a, b: mpmath.sinh(a),
+    Op.COSH: lambda a, b: mpmath.cosh(a), Op.ERF: lambda a, b: mpmath.erf(a),
+    Op.SIGN: lambda a, b: mpmath.sign(a), Op.FLOOR: lambda a, b: mpmath.floor(a),
+    Op.CEIL: lambda a, b: mpmath.ceil(a),
+    Op.FMOD: lambda a, b: mpmath.sign(a) * (abs(a) % abs(b)),  # C fmod: sign of a
+    Op.INV: lambda a, b: 1 / a, Op.HYPOT: lambda a, b: mpmath.hypot(a, b),
+    Op.LOG1P: lambda a, b: mpmath.log1p(a), Op.EXPM1: lambda a, b: mpmath.expm1(a),
+    Op.COPYSIGN: lambda a, b: abs(a) if b >= 0 else -abs(a),
+}
+
+
+@pytest.mark.parametrize("op", sorted(_MPF, key=int), ids=lambda o: o.name)
+def test_single_op_matches_mpmath(op):
+    rng = np.random.default_rng(int(op))
+    lo, hi = _DOMAIN.get(op, (-3.0, 3.0))
+    N = 257
+    x = rng.uniform(lo, hi, size=(2, N))
+    if op in (Op.IF_ELSE_ZERO, Op.AND, Op.OR, Op.NOT, Op.EQ, Op.NE):
+        x[0, ::3] = 0.0
+        x[1, ::5] = x[0, ::5]
+    if op in (Op.DIV, Op.FMOD):
+        x[1] = np.where(np.abs(x[1]) < 0.2, 0.7, x[1])
+    binary = op in BINARY or op == Op.FMA_CONST
+    orc = Oracle(programs.single_op(op).to_bytes())
+    y = orc.eval(x if binary else x[:1])[0]
+    mpmath.mp.dps = 40
+    ref = np.array([float(_MPF[op](mpmath.mpf(x[0, i]), mpmath.mpf(x[1, i]))) for i in range(N)])
+    # libm is not correctly rounded everywhere; allow 2 ulp of the result
+    np.testing.assert_allclose(y, ref, rtol=4.5e-16, atol=1e-300)
+
+
+# ---------------------------------------------------------------------------
+# cart-pole RK4 step + Jacobian
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cartpole():
+    return Oracle(programs.cartpole_rk4().to_bytes())
+
+
+def test_cartpole_equilibrium_is_fixed_point(cartpole):
+    x = np.zeros((5, 7))
+    x[0] = np.linspace(-2, 2, 7)        # cart position is free
+    y = cartpole.eval(x)
+    np.testing.assert_array_equal(y[:4], x[:4])
+
+
+def test_cartpole_jacobian_at_equilibrium_is_rk4_of_linearization(cartpole):
+    x = np.zeros((5, 3))
+    x[0] = [-1.0, 0.0, 0.5]
+    y = cartpole.eval(x)
+    A, B = M.cartpole_linearization()
+    T4, S4B = M.rk4_linear_maps(A, B, 0.01)
+    ref = np.hstack([T4, S4B])
+    for i in range(3):
+        np.testing.assert_allclose(y[4:, i].reshape(4, 5), ref, rtol=0, atol=1e-14)
+
+
+def test_cartpole_matches_hand_derived_step_and_jacobian(cartpole):
+    x = inputs.cartpole(64, seed=0)
+    y = cartpole.eval(x)
+    for i in range(64):
+        qn, J = M.cartpole_rk4_with_jacobian(x[:4, i], x[4, i])
+        np.testing.assert_allclose(y[:4, i], qn, rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(y[4:, i].reshape(4, 5), J, rtol=1e-12, atol=1e-13)
+
+
+def test_cartpole_jacobian_matches_central_differences(cartpole):
+    x = inputs.cartpole(16, seed=3)
+    y = cartpole.eval(x)
+    h = 1e-6
+    for j in range(5):
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fd = (cartpole.eval(xp)[:4] - cartpole.eval(xm)[:4]) / (2 * h)
+        Jcol = y[4:].reshape(4, 5, -1)[:, j, :]
+        np.testing.assert_allclose(Jcol, fd, rtol=1e-7, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# RK4 order: linear oscillator (closed form) and pendulum energy drift
+# ---------------------------------------------------------------------------
+def test_oscillator_rk4_equals_taylor_polynomial():
+    w, dt = 3.0, 0.05
+    orc = Oracle(programs.oscillator_rk4(w, dt).to_bytes())
+    A = np.array([[0.0, 1.0], [-w * w, 0.0]])
+    T4, _ = M.rk4_linear_maps(A, np.zeros((2, 1)), dt)
+    x = inputs.uniform(2, 50, -1, 1, seed=5)
+    np.testing.assert_allclose(orc.eval(x), T4 @ x, rtol=1e-14, atol=1e-15)
+
+
+def test_pendulum_rk4_global_error_is_fourth_order():
+    """Halving dt over a fixed horizon shrinks RK4's global error ~16x; the
+    reference trajectory is an 8th-order adaptive integration (scipy DOP853)."""
+    from scipy.integrate import solve_ivp
+    T_end = 2.0
+    x = np.array([[1.0, 2.0, 0.3], [0.0, 0.5, 1.0]])
+    ref = np.array([solve_ivp(lambda t, s: [s[1], -9.81 * np.sin(s[0])], (0, T_end), x[:, i],
+                              method="DOP853", rtol=1e-13, atol=1e-14).y[:, -1]
+                    for i in range(3)]).T
+    err = []
+    for steps in (100, 200):
+        y = Oracle(programs.pendulum_rk4(steps, T_end / steps).to_bytes()).eval(x)
+        err.append(np.max(np.abs(y - ref), axis=0))
+    ratio = err[0] / err[1]
+    assert np.all(ratio > 13) and np.all(ratio < 19), ratio
+
+
+def test_pendulum_energy_drift_shrinks_at_least_fourth_order():
+    """Energy E = om^2/2 - (g/l) cos th is conserved by the flow; RK4's drift
+    after a fixed horizon falls by >= 2^4 when dt is halved."""
+    x = np.array([[1.0, 0.3], [0.0, 1.0]])
+    E0 = M.pendulum_energy(x[0], x[1])
+    drift = []
+    for steps in (100, 200):
+        y = Oracle(programs.pendulum_rk4(steps, 2.0 / steps).to_bytes()).eval(x)
+        drift.append(np.abs(M.pendulum_energy(y[0], y[1]) - E0))
+    assert np.all(drift[0] / drift[1] > 14), drift
+
+
+# ---------------------------------------------------------------------------
+# random programs: exact value (mpmath) within the rounding bound
+# ---------------------------------------------------------------------------
+def test_random_program_within_rounding_bound_of_exact():
+    ir = programs.random_program(3000, seed=11).to_bytes()
+    orc = Oracle(ir)
+    x = inputs.normal(64, 8, seed=1)
+    y = orc.eval(x)
+    B = orc.rounding_bound(x, kind=0)
+    exact = np.array([[float(v) for v in row] for row in mp_eval(ir, x.tolist(), dps=40)])
+    err = np.abs(y - exact)
+    assert np.all(err <= B + 1e-300), float(np.max(err / np.maximum(B, 1e-300)))
+
+
+def test_fp32_emulation_within_fp32_rounding_bound():
+    ir = programs.random_program(3000, seed=12).to_bytes()
+    orc = Oracle(ir)
+    x = inputs.normal(64, 16, seed=2)
+    y64 = orc.eval(x)
+    y32 = orc.eval(x, mode=MODE_F32)
+    B = orc.rounding_bound(x, kind=1)
+    assert np.all(np.abs(y32 - y64) <= B + np.ldexp(1.0, -24) * np.abs(y64))
+    assert np.any(y32 != y64)
+
+
+def test_fp32_emulation_is_ieee_float_for_basic_ops():
+    """((a + b) * c - d) / sqrt(e) evaluated step by step in numpy float32."""
+    g_in = [Instr(Op.INPUT, j, j) for j in range(5)]
+    body = [Instr(Op.ADD, 5, 0, 1), Instr(Op.MUL, 5, 5, 2), Instr(Op.SUB, 5, 5, 3),
+            Instr(Op.SQRT, 6, 4), Instr(Op.DIV, 5, 5, 6), Instr(Op.OUTPUT, 0, 5)]
+    ir = ProgramIR(7, [Sparsity.dense(5, 1, "x")], [Sparsity.dense(1, 1, "y")], g_in + body, [])
+    x = inputs.uniform(5, 4096, 0.1, 3.0, seed=9).astype(np.float32)
+    y = Oracle(ir.to_bytes()).eval(x.astype(np.float64), mode=MODE_F32)[0]
+    a, b, c, d, e = x
+    ref = ((a + b) * c - d) / np.sqrt(e)
+    assert ref.dtype == np.float32
+    np.testing.assert_array_equal(y, ref.astype(np.float64))
+
+
+def test_tiny_programs_match_symbolic_rederivation():
+    """Brute force: rebuild each tiny program as one sympy expression tree from
+    the instruction list and evaluate it with mpmath."""
+    import sympy
+    for seed in range(6):
+        ir_obj = programs.random_program(18, n_in=4, n_out=3, seed=100 + seed)
+        ir = ir_obj.to_bytes()
+        xs = sympy.symbols("x0:4")
+        w = {}
+        outs = {}
+        fn = {Op.ADD: lambda a, b: a + b, Op.SUB: lambda a, b: a - b, Op.MUL: lambda a, b: a * b,
+              Op.DIV: lambda a, b: a / b, Op.NEG: lambda a, b: -a, Op.SQ: lambda a, b: a ** 2,
+              Op.SQRT: lambda a, b: sympy.sqrt(a), Op.SIN: lambda a, b: sympy.sin(a),
+              Op.COS: lambda a, b: sympy.cos(a), Op.EXP: lambda a, b: sympy.exp(a)}
+        for ins in ir_obj.instrs:
+            if ins.op == Op.INPUT:
+                w[ins.out] = xs[ins.a]
+            elif ins.op == Op.CONST:
+                w[ins.out] = sympy.Float(ir_obj.consts[ins.a], 30)
+            elif ins.op == Op.OUTPUT:
+                outs[ins.out] = w[ins.a]
+            elif ins.op == Op.FMA_CONST:
+                w[ins.out] = sympy.Float(ir_obj.consts[ins.c], 30) * w[ins.a] + w[ins.b]
+            else:
+                w[ins.out] = fn[Op(ins.op)](w[ins.a], w[ins.b])
+        f = sympy.lambdify(xs, [outs[k] for k in range(3)], modules="mpmath")
+        x = inputs.normal(4, 5, seed=seed)
+        y = Oracle(ir).eval(x)
+        mpmath.mp.dps = 30
+        for i in range(5):
+            ref = [float(v) for v in f(*[mpmath.mpf(v) for v in x[:, i]])]
+            np.testing.assert_allclose(y[:, i], ref, rtol=1e-13, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# reverse sweep
+# ---------------------------------------------------------------------------
+def test_adjoint_equals_transpose_of_forward_mode_jacobian(cartpole):
+    """The cart-pole program outputs its own Jacobian (traced by forward mode);
+    the oracle's reverse sweep of q+ must give J^T ybar."""
+    x = inputs.cartpole(32, seed=4)
+    y = cartpole.eval(x)
+    ybar = np.zeros((24, 32))
+    ybar[:4] = np.random.default_rng(0).standard_normal((4, 32))
+    xbar = cartpole.adjoint(x, ybar)
+    for i in range(32):
+        J = y[4:, i].reshape(4, 5)
+        np.testing.assert_allclose(xbar[:, i], J.T @ ybar[:4, i], rtol=1e-12, atol=1e-13)
+
+
+def test_adjoint_matches_central_differences_random_program():
+    ir = programs.random_program(400, n_in=8, n_out=5, seed=21).to_bytes()
+    orc = Oracle(ir)
+    x = inputs.normal(8, 6, seed=3)
+    rng = np.random.default_rng(1)
+    ybar = rng.standard_normal((5, 6))
+    xbar = orc.adjoint(x, ybar)
+    h = 1e-6
+    for k in range(8):
+        xp, xm = x.copy(), x.copy()
+        xp[k] += h
+        xm[k] -= h
+        fd = np.sum((orc.eval(xp) - orc.eval(xm)) / (2 * h) * ybar, axis=0)
+        np.testing.assert_allclose(xbar[k], fd, rtol=2e-6, atol=1e-7)
+
+
+def test_adjoint_dot_product_identity():
+    """<J v, w> = <v, J^T w> with J v from directional central differences."""
+    ir = programs.random_program(300, n_in=6, n_out=4, seed=31).to_bytes()
+    orc = Oracle(ir)
+    x = inputs.normal(6, 4, seed=8)
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal((6, 4))
+    w = rng.standard_normal((4, 4))
+    h = 1e-6
+    Jv = (orc.eval(x + h * v) - orc.eval(x - h * v)) / (2 * h)
+    lhs = np.sum(Jv * w, axis=0)
+    rhs = np.sum(v * orc.adjoint(x, w), axis=0)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-6, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# IR rejection
+# ---------------------------------------------------------------------------
+def test_oracle_rejects_malformed_programs():
+    good = programs.listing2()
+    with pytest.raises(OracleError):
+        Oracle(b"XXXX" + good.to_bytes()[4:])
+    bad = programs.listing2()
+    bad.instrs[1] = Instr(Op.SIN, 1, 5)        # operand slot out of range
+    with pytest.raises(OracleError):
+        Oracle(bad.to_bytes())
+    bad = programs.listing2()
+    bad.instrs = bad.instrs[:-1]               # output never written
+    with pytest.raises(OracleError):
+        Oracle(bad.to_bytes())
+    bad = programs.listing2()
+    bad.instrs.insert(0, Instr(Op.ADD, 1, 0, 1))  # reads slots before they are defined
+    with pytest.raises(OracleError):
+        Oracle(bad.to_bytes())
+    with pytest.raises(OracleError):
+        Oracle(good.to_bytes()[:40])           # truncated
