@@ -1,0 +1,330 @@
+"""Benchmark: batched evaluation of the 20,000-op random straight-line program.
+
+Workload (one step = one evaluation of the whole batch): the seeded random
+program (64 inputs, 32 outputs, 20,000 generated ops with the stated op mix,
+program seed 0) on N = 65,536 instances with N(0, 1) inputs (seed 1 + rank).
+The FP64 kernel is the headline; the FP32 kernel is reported beside it with
+its error against the FP64 oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
+65,536 instances (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("instance-evals/s & Gop/s vs FP32/FP64 peak at N=65536; adjoint/forward time ratio")
+N_INST = 65536
+N_OPS_GEN = 20000
+PROGRAM_SEED, INPUT_SEED = 0, 1
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config(info=None):
+    c = {"workload": "random straight-line program: 20000 generated ops, 64 inputs, 32 outputs, "
+                     "op mix 30% add/sub, 30% mul, 5% div, 10% sin/cos, 10% exp(-x^2), "
+                     "5% sqrt(1+x^2), 10% fma-const; N=65536 instances",
+         "N": N_INST, "ops_generated": N_OPS_GEN, "program_seed": PROGRAM_SEED,
+         "input_seed": INPUT_SEED, "inputs": "N(0,1), synthetic",
+         "l2": "flushed between timed steps (256 MB write, outside the events)"}
+    if info is not None:
+        c["ops_ir"] = int(info.n_ops_ir)
+        c["ops_live"] = int(info.n_ops)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_baseline(ir: bytes, x: np.ndarray, sample: int):
+    from oracle import Oracle
+    orc = Oracle(ir)
+    xs = np.ascontiguousarray(x[:, :sample])
+    cores = os.cpu_count() or 1
+    orc.eval(xs[:, :256], threads=cores)   # warm-up
+    t = time.perf_counter()
+    orc.eval(xs, threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": sample / dt, "unit": "instance-evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample} of the {N_INST} instances, FP64 interpreter, {cores} threads, "
+                      f"{dt:.2f} s wall"}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm, on this host's cores."""
+    from oracle import Oracle
+    from paper_2408_09662_gb300 import inputs, programs
+    if rank != 0:
+        return
+    ir = programs.random_program(N_OPS_GEN, seed=PROGRAM_SEED).to_bytes()
+    orc = Oracle(ir)
+    sample = 8192
+    x = inputs.normal(64, sample, seed=INPUT_SEED)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        orc.eval(x[:, :512], threads=cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        orc.eval(x, threads=cores)
+    dt = time.perf_counter() - t
+    value = sample * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "instance-evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": "instance-evals/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"each step evaluates {sample} of the {N_INST} instances"},
+            "e2e": {"value": value, "unit": "instance-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_2408_09662_gb300 import inputs, peaks, programs
+    from paper_2408_09662_gb300.api import Function
+
+    ir = programs.random_program(N_OPS_GEN, seed=PROGRAM_SEED).to_bytes()
+    with ThreadPoolExecutor(2) as ex:   # the two NVRTC compiles overlap (ctypes drops the GIL)
+        f64_fut = ex.submit(Function, ir, dtype="f64")
+        f32_fut = ex.submit(Function, ir, dtype="f32")
+        fn64, fn32 = f64_fut.result(), f32_fut.result()
+
+    x_np = inputs.normal(64, N_INST, seed=INPUT_SEED + rank)
+    x64 = torch.tensor(x_np, dtype=torch.float64, device=dev)
+    x32 = x64.float()
+    y64 = torch.empty((fn64.nnz_out, N_INST), dtype=torch.float64, device=dev)
+    y32 = torch.empty((fn32.nnz_out, N_INST), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, x, y, steps):
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            fn(x, out=y)
+            e.record(stream)
+            times.append((s, e))
+        return times
+
+    for _ in range(args.warmup):
+        fn64(x64, out=y64)
+        fn32(x32, out=y32)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K FP64 steps ------------------------------------------
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev = timed(fn64, x64, y64, args.steps)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    clocks = clk.summary()
+
+    # ---- FP32 kernel, same protocol ----------------------------------------------
+    ev32 = timed(fn32, x32, y32, args.steps)
+    torch.cuda.synchronize()
+    ms32 = sum(s.elapsed_time(e) for s, e in ev32) / args.steps
+
+    # ---- end to end through the public API: pinned host in, host out ------------
+    xh = x64.cpu().pin_memory()
+    yh = torch.empty((fn64.nnz_out, N_INST), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        x64.copy_(xh, non_blocking=True)
+        fn64(x64, out=y64)
+        yh.copy_(y64, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        x64.copy_(xh, non_blocking=True)
+        fn64(x64, out=y64)
+        yh.copy_(y64, non_blocking=True)
+        e.record(stream)
+        e2e_ev.append((s, e))
+    torch.cuda.synchronize()
+    e2e_ms = sum(s.elapsed_time(e) for s, e in e2e_ev) / args.steps
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- accuracy of the FP32 kernel against the FP64 oracle (sampled) ----------
+    from oracle import Oracle
+    orc = Oracle(ir)
+    idx = np.random.default_rng(0).choice(N_INST, 128, replace=False)
+    x32h = x32.double().cpu().numpy()[:, idx]
+    ref = orc.eval(x32h)
+    y32h = y32.double().cpu().numpy()[:, idx]
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    rel32 = np.abs(y32h - ref) / scale
+    ref64 = orc.eval(x_np[:, idx])
+    rel64 = np.abs(y64.cpu().numpy()[:, idx] - ref64) / np.max(np.abs(ref64), axis=1, keepdims=True)
+
+    # ---- roofline: measured FMA rate and per-op weights -------------------------
+    pk64, pk32 = peaks.measure("f64"), peaks.measure("f32")
+    w64 = peaks.weighted_ops(fn64.op_counts(), pk64["weights"])
+    w32 = peaks.weighted_ops(fn32.op_counts(), pk32["weights"])
+    t64, t32 = ms_per_step * 1e-3, ms32 * 1e-3
+    ach64 = w64 * N_INST / t64
+    ach32 = w32 * N_INST / t32
+    ops_live = fn64.info.n_ops
+    value = world * N_INST / t64
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_oracle_baseline(ir, x_np, N_INST)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "instance-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(fn64.info),
+        "gop_per_s": ops_live * N_INST / t64 * 1e-9,
+        "roofline": {"bound": "alu", "achieved": ach64 * 1e-12, "peak": pk64["fma_per_s"] * 1e-12,
+                     "unit": "TFMA/s (FMA-equivalent ops, FP64)", "frac": ach64 / pk64["fma_per_s"],
+                     "traffic": None,
+                     "peak_source": "measured FP64 FMA-chain rate on this GPU (peaks.py)",
+                     "work_per_instance_fma_eq": w64},
+        "fp32": {"value": world * N_INST / t32, "unit": "instance-evals/s", "ms_per_step": ms32,
+                 "gop_per_s": fn32.info.n_ops * N_INST / t32 * 1e-9,
+                 "roofline": {"bound": "alu", "achieved": ach32 * 1e-12,
+                              "peak": pk32["fma_per_s"] * 1e-12,
+                              "unit": "TFMA/s (FMA-equivalent ops, FP32)",
+                              "frac": ach32 / pk32["fma_per_s"],
+                              "work_per_instance_fma_eq": w32},
+                 "err_vs_fp64_oracle": {"max_rel_scaled": float(rel32.max()),
+                                        "median_rel_scaled": float(np.median(rel32)),
+                                        "frac_within_2e-4": float(np.mean(rel32 <= 2e-4))},
+                 "speedup_vs_fp64": t64 / t32},
+        "f64_err_vs_oracle": {"max_rel_scaled": float(rel64.max()),
+                              "frac_within_1e-12": float(np.mean(rel64 <= 1e-12))},
+        "op_weights_f64": pk64["weights"], "op_weights_f32": pk32["weights"],
+        "compile_seconds": {"f64": fn64.info.compile_seconds, "f32": fn32.info.compile_seconds},
+        "e2e": {"value": world * N_INST / (e2e_ms * 1e-3), "unit": "instance-evals/s",
+                "h2d_bytes_per_step": int(x64.numel() * 8), "d2h_bytes_per_step": int(y64.numel() * 8),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps * fn64.info.n_segments,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "gpu": torch.cuda.get_device_name(dev),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * cusadi.h -- C ABI of the batched straight-line-program engine (libcusadi.so).
+ *
+ * The engine evaluates ONE closed-form symbolic function -- a work vector plus
+ * an ordered list of scalar instructions (CusADi §III-A: each instruction has
+ * an operation id, input slot(s) and an output slot, and the function is
+ * evaluated by traversing the list in order) -- across N independent
+ * instances on the GPU.  Only structural non-zeros of the sparse inputs and
+ * outputs are read and written (§II-A).  Data stays on the GPU: every pointer
+ * passed to the evaluation calls is a device pointer (§III intro: inputs and
+ * outputs are stored only on the GPU).
+ *
+ * Layout of every batched buffer: instance-fastest ("SoA").  Row k of
+ * instance i lives at  buf[k * ld + i]  with ld >= N (elements, not bytes).
+ * The rows of a function's input buffer are the non-zeros of all its input
+ * arguments stacked in argument order (cusadi_arg_info gives each argument's
+ * first row); likewise for outputs.  An input argument flagged BROADCAST holds
+ * one value per non-zero shared by every instance: only column 0 of its rows
+ * is read.
+ *
+ * Element type of the buffers: double for CUSADI_F64, float for CUSADI_F32
+ * and CUSADI_MIXED.
+ *
+ * Errors: every call returns a cusadi_status.  Argument errors are detected on
+ * the host before anything is launched; cusadi_last_error() then returns a
+ * message for the calling thread.  Evaluation calls are asynchronous on the
+ * given stream; they never synchronise the host and never allocate memory.
+ *
+ * Threading: a cusadi_fn is immutable after cusadi_load and may be used from
+ * several host threads and streams at once, provided the workspaces differ.
+ */
+#ifndef CUSADI_H
+#define CUSADI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CUSADI_ABI_VERSION 1
+
+typedef struct cusadi_fn_s* cusadi_fn;        /* one loaded function (library-owned) */
+typedef struct cusadi_batch_s* cusadi_batch;  /* several functions, one launch */
+typedef void* cusadi_stream;                  /* a cudaStream_t / CUstream (NULL = legacy) */
+
+typedef enum {
+  CUSADI_OK = 0,
+  CUSADI_E_INVALID_ARG = 1,  /* a pointer, size, stride or option is unusable */
+  CUSADI_E_INVALID_IR = 2,   /* the program file is malformed or inconsistent */
+  CUSADI_E_COMPILE = 3,      /* NVRTC rejected the generated source */
+  CUSADI_E_CUDA = 4,         /* a CUDA runtime/driver call failed */
+  CUSADI_E_OOM = 5,          /* host allocation failed */
+  CUSADI_E_TIMEOUT = 6,      /* a bounded wait ran out */
+  CUSADI_E_UNSUPPORTED = 7   /* valid request this build does not implement */
+} cusadi_status;
+
+typedef enum { CUSADI_F64 = 0, CUSADI_F32 = 1, CUSADI_MIXED = 2 } cusadi_dtype;
+
+/* Evaluation path.  COMPILED: generated straight-line CUDA kernels (one
+ * instance per thread, values in registers).  INTERP: one precompiled kernel
+ * that walks a packed instruction stream (no compile time; for programs too
+ * large to compile).  AUTO picks COMPILED up to compile_limit_ops. */
+typedef enum { CUSADI_PATH_AUTO = 0, CUSADI_PATH_COMPILED = 1, CUSADI_PATH_INTERP = 2 } cusadi_path;
+
+typedef struct {
+  int32_t dtype;              /* cusadi_dtype                                     (F64) */
+  int32_t path;               /* cusadi_path                                      (AUTO) */
+  int64_t compile_limit_ops;  /* AUTO compiles programs with at most this many ops (300000) */
+  int64_t segment_ops;        /* compiled programs are split into kernels of at most this
+                                 many ops, compiled in parallel                  (40000) */
+  int32_t block;              /* threads per block of compiled kernels, multiple of 32 (128) */
+  int32_t maxrregcount;       /* register cap for compiled kernels, 0 = compiler's choice */
+  int32_t fmad;               /* 1: let the compiler contract a*b+c into fma     (1) */
+  int32_t compile_threads;    /* parallel NVRTC compiles, 0 = all host cores */
+  int32_t schedule;           /* 1: reorder ops to lower register pressure       (1) */
+  int32_t inline_math;        /* 1: inline transcendental functions (slow compile) (0) */
+  int32_t adjoint;            /* 1: build the adjoint kernels at load; 0: at the first call
+                                 that needs them (cusadi_adjoint and friends)   (0) */
+  const char* cache_dir;      /* directory for compiled kernels, NULL = in-memory only */
+} cusadi_options;
+
+typedef struct {
+  int32_t n_in, n_out;        /* argument counts */
+  int64_t nnz_in, nnz_out;    /* stacked non-zero rows of the input / output buffers */
+  int64_t n_instr;            /* instructions in the program file */
+  int64_t n_work;             /* work-vector length in the program file */
+  int64_t n_ops_ir;           /* arithmetic instructions in the program file */
+  int64_t n_ops;              /* arithmetic ops evaluated per instance after the passes */
+  int64_t n_slots;            /* values live at once after scheduling (work slots) */
+  int32_t path;               /* CUSADI_PATH_COMPILED or CUSADI_PATH_INTERP */
+  int32_t n_segments;         /* kernels per evaluation on the compiled path */
+  int32_t dtype;              /* cusadi_dtype */
+  int32_t n_bcast_in;         /* input rows flagged broadcast */
+  double compile_seconds;     /* wall time spent generating and compiling at load */
+} cusadi_fn_info;
+
+typedef struct {
+  uint32_t nrow, ncol, nnz;   /* shape and non-zero count of the sparse argument */
+  uint32_t flags;             /* bit 0: broadcast (inputs only) */
+  int64_t row_offset;         /* first row of this argument in the stacked buffer */
+  const uint32_t* rowptr;     /* CSR row pointers [nrow + 1], owned by the function */
+  const uint32_t* col;        /* CSR column indices [nnz], owned by the function */
+  const char* name;           /* owned by the function */
+} cusadi_arg;
+
+/* Adjoint flags. */
+#define CUSADI_ADJ_ACCUMULATE 1u        /* add into in_bar instead of overwriting it */
+#define CUSADI_ADJ_REDUCE_BROADCAST 2u  /* sum broadcast inputs' adjoints over instances
+                                           into column 0 of their rows */
+
+/* Fills *opt with the defaults quoted above. */
+void cusadi_default_options(cusadi_options* opt);
+
+/* Parses and validates a program (the binary IR of §III-A), runs the passes
+ * (SSA renaming, constant folding, common-subexpression and dead-code
+ * elimination, scheduling for register pressure) and prepares the chosen
+ * path: on the compiled path it generates sm_103a CUDA source and compiles it
+ * with NVRTC (cached by content hash); on the interpreter path it packs the
+ * instruction stream.  Device modules are loaded lazily, on the first
+ * evaluation on each device.  `ir` is copied; the caller keeps it.
+ * opt may be NULL (defaults).  Errors: INVALID_ARG, INVALID_IR, COMPILE, OOM. */
+cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* opt,
+                          cusadi_fn* out);
+
+/* Releases a function and its device modules (call with no evaluation of it
+ * in flight). */
+void cusadi_free(cusadi_fn fn);
+
+cusadi_status cusadi_info(cusadi_fn fn, cusadi_fn_info* out);
+
+/* Description of input (is_output = 0) or output argument `index`. */
+cusadi_status cusadi_arg_info(cusadi_fn fn, int is_output, int index, cusadi_arg* out);
+
+/* counts[op] = number of ops with that IR op code evaluated per instance by the
+ * forward kernels (adjoint = 1: by the adjoint kernels), for op < n. */
+cusadi_status cusadi_op_counts(cusadi_fn fn, int adjoint, int64_t* counts, int n);
+
+/* Bytes of device workspace one evaluation of N instances needs (0 when the
+ * program fits in one kernel).  The caller allocates it, 256-byte aligned. */
+size_t cusadi_workspace_bytes(cusadi_fn fn, int64_t N, int adjoint);
+
+/* y = f(x) for N instances.  in: [nnz_in x ld_in], out: [nnz_out x ld_out]
+ * device buffers of the dtype's element type; ld_in, ld_out >= N (an input
+ * buffer whose rows are all broadcast may use ld_in >= 1).  workspace: at least
+ * cusadi_workspace_bytes(fn, N, 0) bytes, or NULL when that is 0.  N = 0 is a
+ * no-op.  The first call on a device loads the device module (not capturable
+ * in a CUDA graph); later calls only launch kernels on `stream`. */
+cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out,
+                          int64_t ld_out, int64_t N, void* workspace, cusadi_stream stream);
+
+/* Reverse mode: in_bar = J(x)^T out_bar per instance, J = d out / d in.
+ * out_bar: [nnz_out x ld_ob]; in_bar: [nnz_in x ld_ib].  With
+ * CUSADI_ADJ_REDUCE_BROADCAST, broadcast input rows receive the sum over
+ * instances in column 0 (accumulated with atomics, so the summation order and
+ * the last bits vary run to run); otherwise they receive per-instance values.
+ * Without CUSADI_ADJ_ACCUMULATE the written entries are overwritten.
+ * workspace: cusadi_workspace_bytes(fn, N, 1) bytes. */
+cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,
+                             int64_t ld_ob, void* in_bar, int64_t ld_ib, int64_t N,
+                             uint32_t flags, void* workspace, cusadi_stream stream);
+
+/* Writes the generated CUDA source of kernel `segment` (adjoint = 1: of the
+ * adjoint kernels) into buf (NUL-terminated, truncated to *len bytes); sets *len
+ * to the full size + 1.  UNSUPPORTED on the interpreter path. */
+cusadi_status cusadi_source(cusadi_fn fn, int adjoint, int segment, char* buf, size_t* len);
+
+/* Human-readable name of a status, and the last error message of this thread. */
+const char* cusadi_status_string(cusadi_status s);
+const char* cusadi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUSADI_H */

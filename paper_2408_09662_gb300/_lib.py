@@ -1,0 +1,161 @@
+"""ctypes binding of libcusadi.so (include/cusadi.h): same names, argument
+marshalling only.  Every step of an evaluation runs in the library's kernels.
+
+Importing this module never falls back to anything: if libcusadi.so is
+missing or fails to load, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcusadi.so")
+
+c_int32, c_int64, c_uint32, c_size_t = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t
+c_void_p, c_char_p, c_double = ctypes.c_void_p, ctypes.c_char_p, ctypes.c_double
+
+CUSADI_OK = 0
+CUSADI_E_INVALID_ARG = 1
+CUSADI_E_INVALID_IR = 2
+CUSADI_E_COMPILE = 3
+CUSADI_E_CUDA = 4
+CUSADI_E_OOM = 5
+CUSADI_E_TIMEOUT = 6
+CUSADI_E_UNSUPPORTED = 7
+
+CUSADI_F64, CUSADI_F32, CUSADI_MIXED = 0, 1, 2
+CUSADI_PATH_AUTO, CUSADI_PATH_COMPILED, CUSADI_PATH_INTERP = 0, 1, 2
+CUSADI_ADJ_ACCUMULATE = 1
+CUSADI_ADJ_REDUCE_BROADCAST = 2
+
+
+class cusadi_options(ctypes.Structure):
+    _fields_ = [("dtype", c_int32), ("path", c_int32), ("compile_limit_ops", c_int64),
+                ("segment_ops", c_int64), ("block", c_int32), ("maxrregcount", c_int32),
+                ("fmad", c_int32), ("compile_threads", c_int32), ("schedule", c_int32),
+                ("inline_math", c_int32), ("adjoint", c_int32), ("cache_dir", c_char_p)]
+
+
+class cusadi_fn_info(ctypes.Structure):
+    _fields_ = [("n_in", c_int32), ("n_out", c_int32), ("nnz_in", c_int64), ("nnz_out", c_int64),
+                ("n_instr", c_int64), ("n_work", c_int64), ("n_ops_ir", c_int64),
+                ("n_ops", c_int64), ("n_slots", c_int64), ("path", c_int32),
+                ("n_segments", c_int32), ("dtype", c_int32), ("n_bcast_in", c_int32),
+                ("compile_seconds", c_double)]
+
+
+class cusadi_arg(ctypes.Structure):
+    _fields_ = [("nrow", c_uint32), ("ncol", c_uint32), ("nnz", c_uint32), ("flags", c_uint32),
+                ("row_offset", c_int64), ("rowptr", ctypes.POINTER(c_uint32)),
+                ("col", ctypes.POINTER(c_uint32)), ("name", c_char_p)]
+
+
+class CusadiError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = L.cusadi_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {L.cusadi_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+# name -> (restype, argtypes), mirroring include/cusadi.h
+SIGNATURES = {
+    "cusadi_default_options": (None, [ctypes.POINTER(cusadi_options)]),
+    "cusadi_load": (c_int32, [c_void_p, c_size_t, ctypes.POINTER(cusadi_options), ctypes.POINTER(c_void_p)]),
+    "cusadi_free": (None, [c_void_p]),
+    "cusadi_info": (c_int32, [c_void_p, ctypes.POINTER(cusadi_fn_info)]),
+    "cusadi_arg_info": (c_int32, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cusadi_arg)]),
+    "cusadi_op_counts": (c_int32, [c_void_p, ctypes.c_int, ctypes.POINTER(c_int64), ctypes.c_int]),
+    "cusadi_workspace_bytes": (c_size_t, [c_void_p, c_int64, ctypes.c_int]),
+    "cusadi_eval": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
+    "cusadi_adjoint": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
+                                 c_int64, c_uint32, c_void_p, c_void_p]),
+    "cusadi_source": (c_int32, [c_void_p, ctypes.c_int, ctypes.c_int, c_char_p, ctypes.POINTER(c_size_t)]),
+    "cusadi_status_string": (c_char_p, [c_int32]),
+    "cusadi_last_error": (c_char_p, []),
+}
+
+_LIB = None
+
+
+def lib():
+    """The loaded libcusadi.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcusadi.so not built ({LIB_PATH}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def check(status: int, where: str) -> None:
+    if status != CUSADI_OK:
+        raise CusadiError(status, where)
+
+
+# thin same-name wrappers ----------------------------------------------------
+def cusadi_default_options() -> cusadi_options:
+    o = cusadi_options()
+    lib().cusadi_default_options(ctypes.byref(o))
+    return o
+
+
+def cusadi_load(ir: bytes, opt: cusadi_options | None = None) -> int:
+    h = c_void_p()
+    buf = ctypes.create_string_buffer(bytes(ir), len(ir))
+    check(lib().cusadi_load(buf, len(ir), ctypes.byref(opt) if opt is not None else None,
+                            ctypes.byref(h)), "cusadi_load")
+    return h.value
+
+
+def cusadi_free(fn: int) -> None:
+    if fn and _LIB is not None:
+        _LIB.cusadi_free(fn)
+
+
+def cusadi_info(fn: int) -> cusadi_fn_info:
+    i = cusadi_fn_info()
+    check(lib().cusadi_info(fn, ctypes.byref(i)), "cusadi_info")
+    return i
+
+
+def cusadi_arg_info(fn: int, is_output: bool, index: int) -> cusadi_arg:
+    a = cusadi_arg()
+    check(lib().cusadi_arg_info(fn, int(is_output), index, ctypes.byref(a)), "cusadi_arg_info")
+    return a
+
+
+def cusadi_op_counts(fn: int, adjoint: bool = False, n: int = 64) -> list:
+    buf = (c_int64 * n)()
+    check(lib().cusadi_op_counts(fn, int(adjoint), buf, n), "cusadi_op_counts")
+    return list(buf)
+
+
+def cusadi_workspace_bytes(fn: int, N: int, adjoint: bool = False) -> int:
+    return int(lib().cusadi_workspace_bytes(fn, N, int(adjoint)))
+
+
+def cusadi_eval(fn: int, inp: int, ld_in: int, out: int, ld_out: int, N: int, workspace: int,
+                stream: int) -> None:
+    check(lib().cusadi_eval(fn, inp, ld_in, out, ld_out, N, workspace, stream), "cusadi_eval")
+
+
+def cusadi_adjoint(fn: int, inp: int, ld_in: int, out_bar: int, ld_ob: int, in_bar: int,
+                   ld_ib: int, N: int, flags: int, workspace: int, stream: int) -> None:
+    check(lib().cusadi_adjoint(fn, inp, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, flags,
+                               workspace, stream), "cusadi_adjoint")
+
+
+def cusadi_source(fn: int, adjoint: bool = False, segment: int = 0) -> str:
+    n = c_size_t(0)
+    check(lib().cusadi_source(fn, int(adjoint), segment, None, ctypes.byref(n)), "cusadi_source")
+    buf = ctypes.create_string_buffer(n.value)
+    check(lib().cusadi_source(fn, int(adjoint), segment, buf, ctypes.byref(n)), "cusadi_source")
+    return buf.value.decode()

@@ -1,0 +1,153 @@
+"""PyTorch-facing API (CusADi §III-B: torch tensors on the GPU are handed to
+the compiled library; data never leaves the device).
+
+``Function`` wraps one loaded program.  Buffers are torch CUDA tensors of
+shape [rows, N] (row k of instance i at [k, i]); torch supplies memory and the
+current stream, the library does every step of the evaluation.
+"""
+from __future__ import annotations
+
+import os
+
+import torch
+
+from . import _lib as L
+from .ir import ProgramIR
+
+DTYPES = {"f64": L.CUSADI_F64, "f32": L.CUSADI_F32, "mixed": L.CUSADI_MIXED}
+PATHS = {"auto": L.CUSADI_PATH_AUTO, "compiled": L.CUSADI_PATH_COMPILED,
+         "interp": L.CUSADI_PATH_INTERP}
+DEFAULT_CACHE = os.environ.get(
+    "CUSADI_CACHE_DIR",
+    os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build", "kernels"))
+
+
+def _program_bytes(program) -> bytes:
+    if isinstance(program, ProgramIR):
+        return program.to_bytes()
+    if isinstance(program, (bytes, bytearray)):
+        return bytes(program)
+    with open(program, "rb") as f:
+        return f.read()
+
+
+class Function:
+    """A straight-line program loaded into the engine.
+
+    dtype: "f64" | "f32" | "mixed";  path: "auto" | "compiled" | "interp".
+    Other keyword options map onto ``cusadi_options`` fields.
+    """
+
+    def __init__(self, program, dtype: str = "f64", path: str = "auto", cache_dir=DEFAULT_CACHE,
+                 **options):
+        self._fn = None
+        opt = L.cusadi_default_options()
+        opt.dtype = DTYPES[dtype]
+        opt.path = PATHS[path]
+        for k, v in options.items():
+            if not hasattr(opt, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(opt, k, int(v))
+        self._cache = cache_dir.encode() if cache_dir else None
+        if cache_dir:
+            os.makedirs(cache_dir, exist_ok=True)
+        opt.cache_dir = self._cache
+        self.dtype = dtype
+        self._fn = L.cusadi_load(_program_bytes(program), opt)
+        self.info = L.cusadi_info(self._fn)
+        self.nnz_in = self.info.nnz_in
+        self.nnz_out = self.info.nnz_out
+        self.torch_dtype = torch.float64 if dtype == "f64" else torch.float32
+        self.inputs = [L.cusadi_arg_info(self._fn, False, j) for j in range(self.info.n_in)]
+        self.outputs = [L.cusadi_arg_info(self._fn, True, j) for j in range(self.info.n_out)]
+        self._ws = {}
+
+    def __del__(self):
+        if getattr(self, "_fn", None):
+            L.cusadi_free(self._fn)
+            self._fn = None
+
+    @property
+    def handle(self) -> int:
+        return self._fn
+
+    @property
+    def compiled(self) -> bool:
+        return self.info.path == L.CUSADI_PATH_COMPILED
+
+    def op_counts(self, adjoint: bool = False) -> list:
+        return L.cusadi_op_counts(self._fn, adjoint)
+
+    def source(self, adjoint: bool = False, segment: int = 0) -> str:
+        return L.cusadi_source(self._fn, adjoint, segment)
+
+    def workspace(self, N: int, adjoint: bool = False, device=None) -> torch.Tensor | None:
+        nb = L.cusadi_workspace_bytes(self._fn, N, adjoint)
+        if nb == 0:
+            return None
+        key = (adjoint, str(device))
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < nb:
+            ws = torch.empty(nb, dtype=torch.uint8, device=device)
+            self._ws[key] = ws
+        return ws
+
+    def _check(self, t: torch.Tensor, rows: int, name: str):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor (data stays on the GPU)")
+        if t.dtype != self.torch_dtype:
+            raise TypeError(f"{name} must be {self.torch_dtype}, got {t.dtype}")
+        if t.dim() != 2 or t.shape[0] != rows or t.stride(1) != 1:
+            raise ValueError(f"{name} must be [{rows}, N] with unit stride along N")
+
+    def __call__(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """y = f(x).  x: [nnz_in, N]; returns (or fills) y: [nnz_out, N]."""
+        self._check(x, self.nnz_in, "x")
+        N = x.shape[1]
+        if out is None:
+            out = torch.empty((self.nnz_out, N), dtype=self.torch_dtype, device=x.device)
+        self._check(out, self.nnz_out, "out")
+        ws = self.workspace(N, False, x.device)
+        L.cusadi_eval(self._fn, x.data_ptr(), x.stride(0), out.data_ptr(), out.stride(0), N,
+                      ws.data_ptr() if ws is not None else 0,
+                      torch.cuda.current_stream(x.device).cuda_stream)
+        return out
+
+    def adjoint(self, x: torch.Tensor, ybar: torch.Tensor, out: torch.Tensor | None = None,
+                accumulate: bool = False, reduce_broadcast: bool = False) -> torch.Tensor:
+        """x_bar = J(x)^T y_bar per instance (broadcast rows summed when reduce_broadcast)."""
+        self._check(x, self.nnz_in, "x")
+        N = x.shape[1]
+        self._check(ybar, self.nnz_out, "ybar")
+        if out is None:
+            out = (torch.zeros if accumulate else torch.empty)(
+                (self.nnz_in, N), dtype=self.torch_dtype, device=x.device)
+        self._check(out, self.nnz_in, "out")
+        flags = (L.CUSADI_ADJ_ACCUMULATE if accumulate else 0) | \
+                (L.CUSADI_ADJ_REDUCE_BROADCAST if reduce_broadcast else 0)
+        ws = self.workspace(N, True, x.device)
+        L.cusadi_adjoint(self._fn, x.data_ptr(), x.stride(0), ybar.data_ptr(), ybar.stride(0),
+                         out.data_ptr(), out.stride(0), N, flags,
+                         ws.data_ptr() if ws is not None else 0,
+                         torch.cuda.current_stream(x.device).cuda_stream)
+        return out
+
+
+class _Apply(torch.autograd.Function):
+    """y = f(x) with the reverse sweep of the library as its backward."""
+
+    @staticmethod
+    def forward(ctx, fn: Function, x: torch.Tensor):
+        ctx.fn = fn
+        ctx.save_for_backward(x)
+        return fn(x.contiguous())
+
+    @staticmethod
+    def backward(ctx, ybar):
+        (x,) = ctx.saved_tensors
+        return None, ctx.fn.adjoint(x.contiguous(), ybar.contiguous())
+
+
+def apply(fn: Function, x: torch.Tensor) -> torch.Tensor:
+    """Differentiable evaluation (torch.autograd)."""
+    return _Apply.apply(fn, x)

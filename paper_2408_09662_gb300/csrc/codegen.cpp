@@ -1,0 +1,323 @@
+// CUDA source generator: one straight-line kernel body per program segment.
+//
+// CusADi §III-A turns each instruction into one CUDA statement over a global
+// work array (Listing 1, Listing 2).  Here each SSA value becomes a local
+// variable, so the compiler keeps the work vector in registers; inputs are
+// loaded at their first use and outputs stored right after they are computed,
+// all instance-fastest so a warp touches 32 consecutive elements per row.
+// Programs longer than segment_ops are split into several kernels that pass
+// the values live across a cut through a workspace (same SoA layout).
+#include <algorithm>
+#include <cinttypes>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <sstream>
+
+#include "internal.h"
+
+namespace cusadi {
+
+namespace {
+
+std::string lit(double v, bool f64) {
+  char buf[64];
+  if (f64) {
+    if (std::isnan(v)) return "__longlong_as_double(0x7ff8000000000000ll)";
+    if (std::isinf(v)) return v > 0 ? "__longlong_as_double(0x7ff0000000000000ll)"
+                                    : "__longlong_as_double((long long)0xfff0000000000000ull)";
+    std::snprintf(buf, sizeof buf, "%a", v);
+    return std::string("(") + buf + ")";
+  }
+  float f = (float)v;
+  if (std::isnan(f)) return "__int_as_float(0x7fc00000)";
+  if (std::isinf(f)) return f > 0 ? "__int_as_float(0x7f800000)" : "__int_as_float((int)0xff800000u)";
+  std::snprintf(buf, sizeof buf, "%af", (double)f);
+  return std::string("(") + buf + ")";
+}
+
+struct MathFn {
+  const char* d;
+  const char* f;
+};
+
+MathFn math_name(int op) {
+  switch (op) {
+    case EXP: return {"exp", "expf"};
+    case LOG: return {"log", "logf"};
+    case POW: return {"pow", "powf"};
+    case SIN: return {"sin", "sinf"};
+    case COS: return {"cos", "cosf"};
+    case TAN: return {"tan", "tanf"};
+    case ATAN: return {"atan", "atanf"};
+    case ATAN2: return {"atan2", "atan2f"};
+    case TANH: return {"tanh", "tanhf"};
+    case ASIN: return {"asin", "asinf"};
+    case ACOS: return {"acos", "acosf"};
+    case SINH: return {"sinh", "sinhf"};
+    case COSH: return {"cosh", "coshf"};
+    case ERF: return {"erf", "erff"};
+    case FMOD: return {"fmod", "fmodf"};
+    case HYPOT: return {"hypot", "hypotf"};
+    case LOG1P: return {"log1p", "log1pf"};
+    case EXPM1: return {"expm1", "expm1f"};
+    case SQRT: return {"sqrt", "sqrtf"};
+    case FABS: return {"fabs", "fabsf"};
+    case FMIN: return {"fmin", "fminf"};
+    case FMAX: return {"fmax", "fmaxf"};
+    case FLOOR: return {"floor", "floorf"};
+    case CEIL: return {"ceil", "ceilf"};
+    case COPYSIGN: return {"copysign", "copysignf"};
+  }
+  return {"?", "?"};
+}
+
+struct Gen {
+  const Graph& g;
+  const CodegenOptions& o;
+  std::vector<int> seg_of;          // per node (leaves: -1)
+  std::vector<int> last_seg;        // last segment that reads the node
+  std::vector<int64_t> ws_slot;     // workspace row of values crossing a cut
+  std::vector<std::vector<int64_t>> out_rows;  // per node: output rows it feeds
+  std::set<std::pair<int, bool>> calls;        // (op, f64) of out-of-line math used
+
+  Gen(const Graph& g_, const CodegenOptions& o_) : g(g_), o(o_) {}
+
+  bool node_f64(int32_t i) const {
+    if (o.dtype == CUSADI_F64) return true;
+    if (o.dtype == CUSADI_F32) return false;
+    return g.nodes[i].f64 != 0;
+  }
+  const char* ty(bool f64) const { return f64 ? "double" : "float"; }
+  bool buf_f64() const { return o.dtype == CUSADI_F64; }
+  bool ws_f64() const { return o.dtype != CUSADI_F32; }
+  bool leaf(int32_t i) const { return g.nodes[i].op == INPUT || g.nodes[i].op == CONST; }
+};
+
+std::string call_name(int op, bool f64, bool inl) {
+  MathFn m = math_name(op);
+  if (inl) return f64 ? m.d : m.f;
+  return std::string("cs_") + m.d + (f64 ? "_d" : "_f");
+}
+
+}  // namespace
+
+CodegenResult generate(const Graph& g, const CodegenOptions& o) {
+  CodegenResult R;
+  Gen G(g, o);
+  const int64_t n = (int64_t)g.nodes.size();
+  G.seg_of.assign(n, -1);
+  G.last_seg.assign(n, -1);
+  G.out_rows.assign(n, {});
+  for (size_t r = 0; r < g.out.size(); ++r) G.out_rows[g.out[r]].push_back((int64_t)r);
+
+  // segment cuts by op count
+  std::vector<std::pair<int64_t, int64_t>> segs;
+  {
+    int64_t start = 0, ops = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (G.leaf(i)) continue;
+      if (o.segment_ops > 0 && ops >= o.segment_ops) {
+        segs.push_back({start, i});
+        start = i;
+        ops = 0;
+      }
+      ++ops;
+    }
+    segs.push_back({start, n});
+  }
+  const int nseg = (int)segs.size();
+  for (int s = 0; s < nseg; ++s)
+    for (int64_t i = segs[s].first; i < segs[s].second; ++i)
+      if (!G.leaf(i)) G.seg_of[i] = s;
+  for (int64_t i = 0; i < n; ++i) {
+    const Node& x = g.nodes[i];
+    if (G.leaf(i)) continue;
+    for (int32_t a : {x.a, x.b})
+      if (a >= 0 && !G.leaf(a)) G.last_seg[a] = std::max(G.last_seg[a], G.seg_of[i]);
+  }
+  // workspace rows for values read in a later segment; a row is free again for
+  // values defined after the segment of its last reader
+  G.ws_slot.assign(n, -1);
+  {
+    std::vector<std::vector<int64_t>> release(nseg + 1);
+    std::vector<int64_t> free_rows;
+    int64_t rows = 0;
+    for (int s = 0; s < nseg; ++s) {
+      for (int64_t r : release[s > 0 ? s - 1 : nseg]) free_rows.push_back(r);
+      if (s > 0) release[s - 1].clear();
+      for (int64_t i = segs[s].first; i < segs[s].second; ++i) {
+        if (G.leaf(i) || G.last_seg[i] <= s) continue;
+        int64_t r;
+        if (!free_rows.empty()) { r = free_rows.back(); free_rows.pop_back(); }
+        else r = rows++;
+        G.ws_slot[i] = r;
+        release[G.last_seg[i]].push_back(r);
+      }
+    }
+    R.ws_rows = rows;
+  }
+  for (uint8_t f : g.out_reduce) R.has_reduce |= (f != 0);
+
+  const char* tin = G.buf_f64() ? "double" : "float";
+  const char* tw = G.ws_f64() ? "double" : "float";
+
+  for (int s = 0; s < nseg; ++s) {
+    std::ostringstream body;
+    std::vector<uint8_t> have(n, 0);   // leaf or ws value materialised in this segment
+    G.calls.clear();
+    auto operand = [&](int32_t i, bool want_f64) -> std::string {
+      const Node& x = g.nodes[i];
+      bool f = G.node_f64(i);
+      std::string name = "v" + std::to_string(i);
+      if (x.op == CONST) return lit(x.k, want_f64);
+      if (x.op == INPUT) {
+        if (!have[i]) {
+          have[i] = 1;
+          const bool second = o.split >= 0 && x.io >= o.split;
+          const int64_t row = second ? x.io - o.split : x.io;
+          body << "  const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")"
+               << (second ? (x.bcast ? "X2b[" : "X2[") : (x.bcast ? "Xb[" : "X[")) << row
+               << (second ? "ll * ldx2];\n" : "ll * ldx];\n");
+        }
+      } else if (G.seg_of[i] != s) {
+        if (!have[i]) {
+          have[i] = 1;
+          body << "  const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")W["
+               << G.ws_slot[i] << "ll * ldw];\n";
+        }
+      }
+      if (f != want_f64) return std::string("(") + G.ty(want_f64) + ")" + name;
+      return name;
+    };
+    auto store_out = [&](int64_t r, const std::string& v) {
+      if (o.adjoint) {
+        if (g.out_reduce[r]) {
+          body << "  if (reduce) {\n    " << tin << " r_ = active ? (" << tin << ")" << v
+               << " : (" << tin << ")0;\n"
+               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 16);\n"
+               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 8);\n"
+               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 4);\n"
+               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 2);\n"
+               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 1);\n"
+               << "    if ((threadIdx.x & 31u) == 0u) atomicAdd(&Yb[" << r << "ll * ldy], r_);\n"
+               << "  } else if (active) { " << tin << "* p_ = &Y[" << r << "ll * ldy]; *p_ = acc ? *p_ + ("
+               << tin << ")" << v << " : (" << tin << ")" << v << "; }\n";
+        } else {
+          body << "  if (active) { " << tin << "* p_ = &Y[" << r << "ll * ldy]; *p_ = acc ? *p_ + ("
+               << tin << ")" << v << " : (" << tin << ")" << v << "; }\n";
+        }
+      } else {
+        body << "  Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
+      }
+    };
+    // outputs fed directly by inputs or constants are written by segment 0
+    if (s == 0) {
+      for (int64_t i = 0; i < n; ++i) {
+        if (!G.leaf(i) || G.out_rows[i].empty()) continue;
+        std::string v = operand((int32_t)i, G.node_f64((int32_t)i));
+        for (int64_t r : G.out_rows[i]) store_out(r, v);
+      }
+    }
+    for (int64_t i = segs[s].first; i < segs[s].second; ++i) {
+      if (G.leaf(i)) continue;
+      const Node& x = g.nodes[i];
+      const bool f = G.node_f64((int32_t)i);
+      const char* T = G.ty(f);
+      std::string A = x.a >= 0 ? operand(x.a, f) : "";
+      std::string B = x.b >= 0 ? operand(x.b, f) : "";
+      std::string Z = std::string("(") + T + ")0", One = std::string("(") + T + ")1";
+      std::string e;
+      MathFn m = math_name(x.op);
+      const char* mn = f ? m.d : m.f;
+      switch (x.op) {
+        case ADD: e = A + " + " + B; break;
+        case SUB: e = A + " - " + B; break;
+        case MUL: e = A + " * " + B; break;
+        case DIV: e = A + " / " + B; break;
+        case NEG: e = "-" + A; break;
+        case SQ: e = A + " * " + A; break;
+        case INV: e = One + " / " + A; break;
+        case SQRT: case FABS: case FLOOR: case CEIL: e = std::string(mn) + "(" + A + ")"; break;
+        case FMIN: case FMAX: case COPYSIGN: e = std::string(mn) + "(" + A + ", " + B + ")"; break;
+        case FMA_CONST: e = std::string(f ? "fma(" : "fmaf(") + lit(x.k, f) + ", " + A + ", " + B + ")"; break;
+        case IF_ELSE_ZERO: e = "(" + A + " != " + Z + " ? " + B + " : " + Z + ")"; break;
+        case LT: e = "(" + A + " < " + B + " ? " + One + " : " + Z + ")"; break;
+        case LE: e = "(" + A + " <= " + B + " ? " + One + " : " + Z + ")"; break;
+        case EQ: e = "(" + A + " == " + B + " ? " + One + " : " + Z + ")"; break;
+        case NE: e = "(" + A + " != " + B + " ? " + One + " : " + Z + ")"; break;
+        case NOT: e = "(" + A + " == " + Z + " ? " + One + " : " + Z + ")"; break;
+        case AND: e = "((" + A + " != " + Z + " && " + B + " != " + Z + ") ? " + One + " : " + Z + ")"; break;
+        case OR: e = "((" + A + " != " + Z + " || " + B + " != " + Z + ") ? " + One + " : " + Z + ")"; break;
+        case SIGN: e = "(" + A + " > " + Z + " ? " + One + " : (" + A + " < " + Z + " ? -" + One + " : " + Z + "))"; break;
+        default:
+          if (op_call(x.op)) {
+            G.calls.insert({x.op, f});
+            e = call_name(x.op, f, o.inline_math) + "(" + A + (op_arity(x.op) == 2 ? ", " + B : "") + ")";
+          } else {
+            e = "/* unsupported op */ " + Z;
+          }
+      }
+      body << "  const " << T << " v" << i << " = " << e << ";\n";
+      if (G.ws_slot[i] >= 0)
+        body << "  if (active) W[" << G.ws_slot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
+      for (int64_t r : G.out_rows[i]) store_out(r, "v" + std::to_string(i));
+    }
+
+    std::ostringstream src;
+    src << "// Generated straight-line kernel: segment " << s << " of " << nseg
+        << (o.adjoint ? " (adjoint)" : "") << ", dtype "
+        << (o.dtype == CUSADI_F64 ? "f64" : (o.dtype == CUSADI_F32 ? "f32" : "mixed")) << "\n";
+    if (!o.inline_math) {
+      for (auto& c : G.calls) {
+        MathFn m = math_name(c.first);
+        const char* t = c.second ? "double" : "float";
+        bool bin = op_arity(c.first) == 2;
+        src << "static __device__ __noinline__ " << t << " " << call_name(c.first, c.second, false) << "("
+            << t << " a" << (bin ? std::string(", ") + t + " b" : "") << ") { return "
+            << (c.second ? m.d : m.f) << "(a" << (bin ? ", b" : "") << "); }\n";
+      }
+    }
+    std::string name = o.prefix + "_" + std::to_string(s);
+    src << "extern \"C\" __global__ void __launch_bounds__(" << o.block << ") " << name << "(\n"
+        << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
+        << "* __restrict__ X2, long long ldx2, " << tin
+        << "* __restrict__ Y, long long ldy,\n    long long N, " << tw
+        << "* __restrict__ W, long long ldw, int acc, int reduce) {\n"
+        << "  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n";
+    if (o.adjoint) {
+      src << "  const bool active = i0 < N;\n"
+          << "  const long long i = active ? i0 : N - 1;\n";
+    } else {
+      src << "  if (i0 >= N) return;\n  const bool active = true;\n  const long long i = i0;\n";
+    }
+    src << "  const " << tin << "* __restrict__ Xb = X;\n"
+        << "  const " << tin << "* __restrict__ X2b = X2;\n"
+        << "  " << tin << "* __restrict__ Yb = Y;\n"
+        << "  X += i; X2 += i; Y += i; W += i;\n"
+        << "  (void)Xb; (void)X2b; (void)Yb; (void)W; (void)ldw; (void)ldx2; (void)acc; (void)reduce; (void)active;\n"
+        << body.str() << "}\n";
+    Segment S;
+    S.begin = segs[s].first;
+    S.end = segs[s].second;
+    S.name = name;
+    S.source = src.str();
+    R.segs.push_back(std::move(S));
+  }
+  if (R.has_reduce) {
+    // clears the reduced rows (column 0) before an overwriting adjoint
+    std::ostringstream z;
+    R.zero_kernel = o.prefix + "_zero";
+    z << "extern \"C\" __global__ void " << R.zero_kernel << "(" << tin << "* Y, long long ldy) {\n"
+      << "  if (blockIdx.x != 0 || threadIdx.x != 0) return;\n";
+    for (size_t r = 0; r < g.out_reduce.size(); ++r)
+      if (g.out_reduce[r]) z << "  Y[" << r << "ll * ldy] = (" << tin << ")0;\n";
+    z << "}\n";
+    R.segs[0].source += z.str();
+  }
+  return R;
+}
+
+}  // namespace cusadi

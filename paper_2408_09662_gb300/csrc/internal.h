@@ -1,0 +1,135 @@
+// Internal declarations of libcusadi: IR, SSA graph, passes, code generation.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cusadi.h"
+
+namespace cusadi {
+
+// Op codes of the program file (numbering is this project's own; the op set
+// follows the atomic operations CusADi §II-A and Listing 1 name).
+enum Op : uint16_t {
+  INPUT = 0, OUTPUT, CONST, ASSIGN, ADD, SUB, MUL, DIV, NEG, EXP, LOG, POW, SQ, SQRT, SIN,
+  COS, TAN, ATAN, ATAN2, TANH, FABS, FMIN, FMAX, FMA_CONST, IF_ELSE_ZERO, LT, LE, EQ, NE,
+  NOT, AND, OR, ASIN, ACOS, SINH, COSH, ERF, SIGN, FLOOR, CEIL, FMOD, INV, HYPOT, LOG1P,
+  EXPM1, COPYSIGN, N_OPS
+};
+
+int op_arity(int op);            // slot operands: 0 (INPUT/CONST/OUTPUT), 1 or 2
+bool op_commutative(int op);
+bool op_call(int op);            // evaluated through an out-of-line math function
+const char* op_name(int op);
+
+struct Arg {
+  uint32_t nrow = 0, ncol = 0, nnz = 0, flags = 0;
+  std::string name;
+  std::vector<uint32_t> rowptr, col;
+  int64_t offset = 0;            // first stacked row
+};
+
+struct IRInstr {
+  uint16_t op, flags;
+  uint32_t out, a, b, c;
+};
+
+struct IRFile {
+  uint32_t n_work = 0;
+  std::vector<Arg> in, out;
+  std::vector<IRInstr> code;
+  std::vector<double> k;
+  int64_t nnz_in = 0, nnz_out = 0, n_ops = 0;
+};
+
+// Parses and validates; on failure returns false with a message.
+bool parse_ir(const uint8_t* p, size_t n, IRFile& f, std::string& err);
+
+// SSA node.  Operands refer to earlier nodes.
+struct Node {
+  uint16_t op = CONST;
+  uint8_t f64 = 0;               // FP64 tag (mixed precision)
+  uint8_t bcast = 0;             // INPUT from a broadcast row
+  int32_t a = -1, b = -1;
+  double k = 0;                  // CONST value, FMA_CONST literal
+  int64_t io = 0;                // INPUT: stacked input row
+};
+
+struct Graph {
+  std::vector<Node> nodes;       // topological order = evaluation order
+  std::vector<int32_t> out;      // node of each stacked output row
+  std::vector<uint8_t> out_reduce;  // per output row: summed over instances (adjoint)
+  std::vector<uint8_t> in_bcast;    // per stacked input row: broadcast
+  int64_t nnz_in = 0;
+};
+
+Graph build_ssa(const IRFile& f);
+// Constant folding, exact identities, CSE, DCE.  Renumbers nodes.
+void simplify(Graph& g, int dtype);
+// Reorders nodes to lower the number of simultaneously live values.
+void schedule(Graph& g);
+// Reverse-mode transform: inputs [x (nnz_in rows); y_bar (nnz_out rows)],
+// outputs x_bar (nnz_in rows); broadcast x rows are marked out_reduce.
+Graph adjoint_graph(const Graph& g);
+
+// last_use[i]: position of the last reader (or output store) of node i, -1 if none.
+std::vector<int64_t> last_uses(const Graph& g);
+int64_t max_live(const Graph& g);
+int64_t count_ops(const Graph& g);
+void op_histogram(const Graph& g, std::vector<int64_t>& h);
+
+// --- code generation -------------------------------------------------------
+struct Segment {
+  int64_t begin = 0, end = 0;    // node positions [begin, end)
+  std::string name;
+  std::string source;
+};
+
+struct CodegenResult {
+  std::vector<Segment> segs;
+  int64_t ws_rows = 0;           // workspace rows (values carried between segments)
+  bool has_reduce = false;
+  std::string zero_kernel;       // name of the kernel that clears reduced rows
+};
+
+struct CodegenOptions {
+  int dtype = CUSADI_F64;
+  int block = 128;
+  int64_t segment_ops = 40000;
+  bool inline_math = false;
+  bool adjoint = false;
+  int64_t split = -1;            // input rows >= split come from the second buffer
+  std::string prefix = "cs_fwd";
+};
+
+CodegenResult generate(const Graph& g, const CodegenOptions& o);
+
+// --- interpreter stream -------------------------------------------------------
+// code = op | f64 << 7 | bcast << 6 ... packed per instruction (see kernels.cu)
+struct IOp {
+  uint32_t code;   // bits 0..6 op, bit 7 f64 tag, bits 8..31 aux (input row / const / output row)
+  uint32_t out;    // destination slot (OUTPUT: unused)
+  uint32_t a, b;   // operand slots
+};
+
+struct InterpProgram {
+  std::vector<IOp> ops;
+  std::vector<double> k;
+  std::vector<uint8_t> in_bcast;
+  int64_t n_slots = 0;
+  bool has_reduce = false;
+};
+
+bool pack_interp(const Graph& g, InterpProgram& p, std::string& err);
+
+// launchers implemented in kernels.cu.  Input rows >= split are read from X2
+// (row - split); returns a cudaError_t value.
+int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, const void* X,
+                  int64_t ldx, const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy,
+                  int64_t N, void* W, int64_t ldw, int64_t n_slots, int acc, int reduce,
+                  void* stream);
+// threads per block of the shared-memory interpreter (0: work vector too long)
+int interp_block(int64_t n_slots, int dtype);
+
+}  // namespace cusadi

@@ -1,0 +1,165 @@
+// Interpreter kernel: one thread per instance walks a packed instruction
+// stream (the sequential traversal of CusADi §III-A), for programs that are too
+// large to compile.  Every thread reads the same instruction at the same time,
+// so the switch below never diverges within a warp.  The work vector lives in
+// shared memory (slot-major, one column per thread: conflict-free) when it
+// fits, else in a global workspace in the instance-fastest layout.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace cusadi {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T eval_op(uint32_t op, T a, T b, T k) {
+  const T Z = T(0), O = T(1);
+  switch (op) {
+    case ADD: return a + b;
+    case SUB: return a - b;
+    case MUL: return a * b;
+    case DIV: return a / b;
+    case NEG: return -a;
+    case EXP: return exp(a);
+    case LOG: return log(a);
+    case POW: return pow(a, b);
+    case SQ: return a * a;
+    case SQRT: return sqrt(a);
+    case SIN: return sin(a);
+    case COS: return cos(a);
+    case TAN: return tan(a);
+    case ATAN: return atan(a);
+    case ATAN2: return atan2(a, b);
+    case TANH: return tanh(a);
+    case FABS: return fabs(a);
+    case FMIN: return fmin(a, b);
+    case FMAX: return fmax(a, b);
+    case FMA_CONST: return fma(k, a, b);
+    case IF_ELSE_ZERO: return a != Z ? b : Z;
+    case LT: return a < b ? O : Z;
+    case LE: return a <= b ? O : Z;
+    case EQ: return a == b ? O : Z;
+    case NE: return a != b ? O : Z;
+    case NOT: return a == Z ? O : Z;
+    case AND: return (a != Z && b != Z) ? O : Z;
+    case OR: return (a != Z || b != Z) ? O : Z;
+    case ASIN: return asin(a);
+    case ACOS: return acos(a);
+    case SINH: return sinh(a);
+    case COSH: return cosh(a);
+    case ERF: return erf(a);
+    case SIGN: return a > Z ? O : (a < Z ? -O : Z);
+    case FLOOR: return floor(a);
+    case CEIL: return ceil(a);
+    case FMOD: return fmod(a, b);
+    case INV: return O / a;
+    case HYPOT: return hypot(a, b);
+    case LOG1P: return log1p(a);
+    case EXPM1: return expm1(a);
+    case COPYSIGN: return copysign(a, b);
+    case ASSIGN: return a;
+  }
+  return Z;
+}
+
+// B: buffer element type; S: work-slot type; MIXED: per-op precision tags.
+template <typename B, typename S, bool MIXED, bool SMEM>
+__global__ void __launch_bounds__(256) interp_kernel(
+    const uint4* __restrict__ ops, long long n_ops, const double* __restrict__ K,
+    const B* __restrict__ X, long long ldx, const B* __restrict__ X2, long long ldx2,
+    long long split, B* __restrict__ Y, long long ldy, long long N, S* __restrict__ W,
+    long long ldw, int acc, int reduce) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i0 < N;
+  const long long ix = active ? i0 : N - 1;  // inactive lanes read a valid column
+  S* w = SMEM ? reinterpret_cast<S*>(smem_raw) + threadIdx.x : W + i0;
+  const long long ws = SMEM ? (long long)blockDim.x : ldw;
+  for (long long t = 0; t < n_ops; ++t) {
+    const uint4 o = __ldg(&ops[t]);
+    const uint32_t op = o.x & 127u;
+    const long long aux = (long long)(o.x >> 8);
+    if (op == INPUT) {
+      const long long col = o.w ? 0 : ix;
+      w[o.y * ws] = aux < split ? (S)X[aux * ldx + col] : (S)X2[(aux - split) * ldx2 + col];
+      continue;
+    }
+    if (op == CONST) {
+      w[o.y * ws] = (S)K[aux];
+      continue;
+    }
+    if (op == OUTPUT) {
+      B v = (B)w[o.z * ws];
+      if (o.w && reduce) {
+        B r = active ? v : B(0);
+        for (int d = 16; d > 0; d >>= 1) r += __shfl_xor_sync(0xffffffffu, r, d);
+        if ((threadIdx.x & 31u) == 0u) atomicAdd(&Y[aux * ldy], r);
+      } else if (active) {
+        B* p = &Y[aux * ldy + i0];
+        *p = acc ? *p + v : v;
+      }
+      continue;
+    }
+    const S a = w[o.z * ws], b = w[o.w * ws];
+    const double kd = op == FMA_CONST ? K[aux] : 0.0;
+    S r;
+    if (!MIXED || ((o.x >> 7) & 1u)) {
+      r = eval_op<S>(op, a, b, (S)kd);
+    } else {
+      r = (S)eval_op<float>(op, (float)a, (float)b, (float)kd);
+    }
+    w[o.y * ws] = r;
+  }
+}
+
+template <typename B, typename S, bool MIXED, bool SMEM>
+int launch(const IOp* ops, int64_t n_ops, const double* k, const void* X, int64_t ldx,
+           const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy, int64_t N, void* W,
+           int64_t ldw, int64_t n_slots, int block, int acc, int reduce, cudaStream_t st) {
+  auto kern = interp_kernel<B, S, MIXED, SMEM>;
+  size_t smem = SMEM ? (size_t)n_slots * block * sizeof(S) : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  long long grid = (N + block - 1) / block;
+  kern<<<(unsigned)grid, block, smem, st>>>(reinterpret_cast<const uint4*>(ops), n_ops, k,
+                                            (const B*)X, ldx, (const B*)X2, ldx2, split, (B*)Y,
+                                            ldy, N, (S*)W, ldw, acc, reduce);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+// Threads per block for the shared-memory work vector (0: it does not fit).
+int interp_block(int64_t n_slots, int dtype) {
+  const size_t elt = dtype == CUSADI_F32 ? 4 : 8;
+  const size_t budget = 200 * 1024;
+  for (int b = 128; b >= 32; b -= 32)
+    if ((size_t)n_slots * b * elt <= budget) return b;
+  return 0;
+}
+
+int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, const void* X,
+                  int64_t ldx, const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy,
+                  int64_t N, void* W, int64_t ldw, int64_t n_slots, int acc, int reduce,
+                  void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int b = interp_block(n_slots, dtype);
+  const bool smem = b > 0;
+  if (!smem) b = 128;
+  if (dtype == CUSADI_F64)
+    return smem ? launch<double, double, false, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st)
+                : launch<double, double, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st);
+  if (dtype == CUSADI_F32)
+    return smem ? launch<float, float, false, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st)
+                : launch<float, float, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st);
+  return smem ? launch<float, double, true, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st)
+              : launch<float, double, true, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st);
+}
+
+}  // namespace cusadi

@@ -1,0 +1,612 @@
+// Runtime and C ABI of libcusadi: load (parse, passes, code generation, NVRTC
+// compile with a content-hash cache), lazy per-device module loading, and the
+// asynchronous evaluation calls.  Compiling generated code once and calling it
+// from PyTorch on GPU-resident tensors is the CusADi workflow (§III-A end,
+// §III-B); here the compile happens at load time through NVRTC instead of an
+// offline toolkit run.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <thread>
+#include <unordered_map>
+
+#include "internal.h"
+
+using namespace cusadi;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+cusadi_status fail(cusadi_status s, const std::string& msg) {
+  t_last_error = msg;
+  return s;
+}
+
+uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
+  const uint8_t* b = (const uint8_t*)p;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+std::mutex g_cache_mu;
+std::unordered_map<uint64_t, std::string> g_cubins;  // content hash -> cubin
+
+bool compile_nvrtc(const std::string& src, const std::string& name,
+                   const std::vector<std::string>& opts, const char* cache_dir, std::string& cubin,
+                   std::string& log) {
+  int vmaj = 0, vmin = 0;
+  nvrtcVersion(&vmaj, &vmin);
+  uint64_t h = fnv1a(src.data(), src.size());
+  for (auto& o : opts) h = fnv1a(o.data(), o.size() + 1, h);
+  h = fnv1a(&vmaj, sizeof vmaj, h);
+  h = fnv1a(&vmin, sizeof vmin, h);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cubins.find(h);
+    if (it != g_cubins.end()) { cubin = it->second; return true; }
+  }
+  char hex[32];
+  std::snprintf(hex, sizeof hex, "%016llx", (unsigned long long)h);
+  std::string path = cache_dir && *cache_dir ? std::string(cache_dir) + "/cs_" + hex + ".cubin" : "";
+  if (!path.empty()) {
+    std::ifstream f(path, std::ios::binary);
+    if (f) {
+      std::ostringstream ss;
+      ss << f.rdbuf();
+      cubin = ss.str();
+      if (!cubin.empty()) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        g_cubins[h] = cubin;
+        return true;
+      }
+    }
+  }
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), (name + ".cu").c_str(), 0, nullptr, nullptr) !=
+      NVRTC_SUCCESS) {
+    log = "nvrtcCreateProgram failed";
+    return false;
+  }
+  std::vector<const char*> o;
+  for (auto& s : opts) o.push_back(s.c_str());
+  nvrtcResult rc = nvrtcCompileProgram(prog, (int)o.size(), o.data());
+  size_t ls = 0;
+  nvrtcGetProgramLogSize(prog, &ls);
+  if (ls > 1) {
+    log.resize(ls);
+    nvrtcGetProgramLog(prog, &log[0]);
+  }
+  if (rc != NVRTC_SUCCESS) {
+    log = std::string(nvrtcGetErrorString(rc)) + ": " + log;
+    nvrtcDestroyProgram(&prog);
+    return false;
+  }
+  size_t cs = 0;
+  nvrtcGetCUBINSize(prog, &cs);
+  cubin.resize(cs);
+  nvrtcGetCUBIN(prog, &cubin[0]);
+  nvrtcDestroyProgram(&prog);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cubins[h] = cubin;
+  }
+  if (!path.empty()) {
+    std::string tmp = path + ".tmp" + std::to_string((unsigned long long)std::hash<std::thread::id>()(std::this_thread::get_id()));
+    std::ofstream f(tmp, std::ios::binary);
+    if (f) {
+      f.write(cubin.data(), (std::streamsize)cubin.size());
+      f.close();
+      std::rename(tmp.c_str(), path.c_str());
+    }
+  }
+  return true;
+}
+
+// Driver-API entry points, fetched through the runtime so that the library
+// does not link libcuda (it must load on machines without a GPU driver).
+struct Driver {
+  CUresult (*moduleLoadData)(CUmodule*, const void*) = nullptr;
+  CUresult (*moduleGetFunction)(CUfunction*, CUmodule, const char*) = nullptr;
+  CUresult (*moduleUnload)(CUmodule) = nullptr;
+  CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                           unsigned, CUstream, void**, void**) = nullptr;
+  bool ok = false;
+};
+
+const Driver& driver() {
+  static Driver d;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    auto get = [](const char* sym, void** fp) {
+      cudaDriverEntryPointQueryResult q;
+      return cudaGetDriverEntryPointByVersion(sym, fp, 12000, cudaEnableDefault, &q) ==
+                 cudaSuccess &&
+             q == cudaDriverEntryPointSuccess && *fp != nullptr;
+    };
+    d.ok = get("cuModuleLoadData", (void**)&d.moduleLoadData) &&
+           get("cuModuleGetFunction", (void**)&d.moduleGetFunction) &&
+           get("cuModuleUnload", (void**)&d.moduleUnload) &&
+           get("cuLaunchKernel", (void**)&d.launchKernel);
+  });
+  return d;
+}
+
+struct DevState {
+  bool fwd_ready = false, adj_ready = false;
+  std::vector<CUmodule> mods;
+  std::vector<CUfunction> fwd, adj;
+  CUfunction adj_zero = nullptr;
+  void* d_ops_fwd = nullptr;
+  double* d_k_fwd = nullptr;
+  void* d_ops_adj = nullptr;
+  double* d_k_adj = nullptr;
+};
+
+// One compiled or packed evaluation direction (forward or adjoint).
+struct Direction {
+  Graph g;
+  int64_t n_ops = 0, n_slots = 0;
+  std::vector<int64_t> hist;
+  CodegenResult cg;
+  std::vector<std::string> bins;
+  InterpProgram ip;
+};
+
+}  // namespace
+
+struct cusadi_fn_s {
+  cusadi_options opt;
+  std::string cache_dir;
+  IRFile ir;
+  int path = CUSADI_PATH_COMPILED;
+  Direction fwd;
+  std::mutex adj_mu;
+  bool adj_built = false;
+  cusadi_status adj_status = CUSADI_OK;
+  std::string adj_error;
+  Direction adj;
+  double compile_seconds = 0;
+  std::mutex dev_mu;
+  std::map<int, DevState> dev;
+};
+
+namespace {
+
+std::vector<std::string> nvrtc_options(const cusadi_options& o) {
+  std::vector<std::string> v = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo",
+                                "-DNDEBUG"};
+  v.push_back(o.fmad ? "--fmad=true" : "--fmad=false");
+  if (o.maxrregcount > 0) v.push_back("--maxrregcount=" + std::to_string(o.maxrregcount));
+  return v;
+}
+
+cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
+  CodegenOptions co;
+  co.dtype = fn->opt.dtype;
+  co.block = fn->opt.block;
+  co.segment_ops = fn->opt.segment_ops;
+  co.inline_math = fn->opt.inline_math != 0;
+  co.adjoint = adjoint;
+  co.split = adjoint ? fn->ir.nnz_in : -1;
+  co.prefix = adjoint ? "cs_adj" : "cs_fwd";
+  d.cg = generate(d.g, co);
+  const size_t ns = d.cg.segs.size();
+  d.bins.assign(ns, std::string());
+  std::vector<std::string> logs(ns);
+  std::vector<uint8_t> ok(ns, 0);
+  auto opts = nvrtc_options(fn->opt);
+  int nt = fn->opt.compile_threads > 0 ? fn->opt.compile_threads
+                                       : (int)std::max(1u, std::thread::hardware_concurrency());
+  nt = (int)std::min<size_t>((size_t)nt, ns);
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    for (size_t s; (s = next.fetch_add(1)) < ns;)
+      ok[s] = compile_nvrtc(d.cg.segs[s].source, d.cg.segs[s].name, opts,
+                            fn->cache_dir.empty() ? nullptr : fn->cache_dir.c_str(), d.bins[s],
+                            logs[s]);
+  };
+  if (nt <= 1) work();
+  else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(work);
+    for (auto& t : th) t.join();
+  }
+  for (size_t s = 0; s < ns; ++s)
+    if (!ok[s]) return fail(CUSADI_E_COMPILE, "NVRTC failed on " + d.cg.segs[s].name + ": " + logs[s].substr(0, 4000));
+  return CUSADI_OK;
+}
+
+cusadi_status prepare_direction(cusadi_fn fn, Direction& d, bool adjoint) {
+  simplify(d.g, fn->opt.dtype);
+  if (fn->opt.schedule) schedule(d.g);
+  d.n_ops = count_ops(d.g);
+  d.n_slots = max_live(d.g);
+  op_histogram(d.g, d.hist);
+  if (fn->path == CUSADI_PATH_INTERP) {
+    std::string err;
+    if (!pack_interp(d.g, d.ip, err)) return fail(CUSADI_E_UNSUPPORTED, err);
+    d.n_slots = d.ip.n_slots;
+    return CUSADI_OK;
+  }
+  return compile_direction(fn, d, adjoint);
+}
+
+cusadi_status ensure_adjoint(cusadi_fn fn) {
+  std::lock_guard<std::mutex> lk(fn->adj_mu);
+  if (fn->adj_built) {
+    if (fn->adj_status != CUSADI_OK) t_last_error = fn->adj_error;
+    return fn->adj_status;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  fn->adj.g = adjoint_graph(fn->fwd.g);
+  fn->adj_status = prepare_direction(fn, fn->adj, true);
+  if (fn->adj_status != CUSADI_OK) fn->adj_error = t_last_error;
+  fn->compile_seconds +=
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  fn->adj_built = true;
+  return fn->adj_status;
+}
+
+cusadi_status cuda_fail(const char* what, int code) {
+  return fail(CUSADI_E_CUDA, std::string(what) + " failed with code " + std::to_string(code));
+}
+
+// Loads the direction's modules (or uploads its instruction stream) on the
+// current device.  Called with fn->dev_mu held.
+cusadi_status load_on_device(cusadi_fn fn, DevState& ds, bool adjoint) {
+  cudaError_t ce = cudaFree(nullptr);  // makes the device's primary context current
+  if (ce != cudaSuccess) return fail(CUSADI_E_CUDA, std::string("CUDA init: ") + cudaGetErrorString(ce));
+  if (!driver().ok) return fail(CUSADI_E_CUDA, "CUDA driver entry points unavailable");
+  Direction& d = adjoint ? fn->adj : fn->fwd;
+  if (fn->path == CUSADI_PATH_INTERP) {
+    void* ops = nullptr;
+    double* k = nullptr;
+    size_t ob = std::max<size_t>(d.ip.ops.size(), 1) * sizeof(IOp);
+    size_t kb = std::max<size_t>(d.ip.k.size(), 1) * sizeof(double);
+    if ((ce = cudaMalloc(&ops, ob)) != cudaSuccess) return cuda_fail("cudaMalloc", ce);
+    if ((ce = cudaMalloc((void**)&k, kb)) != cudaSuccess) { cudaFree(ops); return cuda_fail("cudaMalloc", ce); }
+    if (!d.ip.ops.empty()) cudaMemcpy(ops, d.ip.ops.data(), d.ip.ops.size() * sizeof(IOp), cudaMemcpyHostToDevice);
+    if (!d.ip.k.empty()) cudaMemcpy(k, d.ip.k.data(), d.ip.k.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if ((ce = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail("upload", ce);
+    (adjoint ? ds.d_ops_adj : ds.d_ops_fwd) = ops;
+    (adjoint ? ds.d_k_adj : ds.d_k_fwd) = k;
+  } else {
+    std::vector<CUfunction>& fs = adjoint ? ds.adj : ds.fwd;
+    fs.clear();
+    for (size_t s = 0; s < d.bins.size(); ++s) {
+      CUmodule m;
+      CUresult r = driver().moduleLoadData(&m, d.bins[s].data());
+      if (r != CUDA_SUCCESS) return cuda_fail("cuModuleLoadData", r);
+      ds.mods.push_back(m);
+      CUfunction f;
+      r = driver().moduleGetFunction(&f, m, d.cg.segs[s].name.c_str());
+      if (r != CUDA_SUCCESS) return cuda_fail("cuModuleGetFunction", r);
+      fs.push_back(f);
+      if (s == 0 && adjoint && d.cg.has_reduce) {
+        r = driver().moduleGetFunction(&ds.adj_zero, m, d.cg.zero_kernel.c_str());
+        if (r != CUDA_SUCCESS) return cuda_fail("cuModuleGetFunction", r);
+      }
+    }
+  }
+  (adjoint ? ds.adj_ready : ds.fwd_ready) = true;
+  return CUSADI_OK;
+}
+
+cusadi_status device_state(cusadi_fn fn, bool adjoint, DevState** out) {
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(CUSADI_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+  std::lock_guard<std::mutex> lk(fn->dev_mu);
+  DevState& ds = fn->dev[dev];
+  if (!(adjoint ? ds.adj_ready : ds.fwd_ready)) {
+    cusadi_status s = load_on_device(fn, ds, adjoint);
+    if (s != CUSADI_OK) return s;
+  }
+  *out = &ds;
+  return CUSADI_OK;
+}
+
+size_t elt_io(int dtype) { return dtype == CUSADI_F64 ? 8 : 4; }
+size_t elt_ws(int dtype) { return dtype == CUSADI_F32 ? 4 : 8; }
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int64_t interp_ldw(int64_t N) { return round_up(std::max<int64_t>(N, 1), 128); }
+
+size_t direction_ws(cusadi_fn fn, const Direction& d, int64_t N) {
+  if (N <= 0) return 0;
+  if (fn->path == CUSADI_PATH_INTERP) {
+    if (interp_block(d.ip.n_slots, fn->opt.dtype) > 0) return 0;
+    return (size_t)d.ip.n_slots * interp_ldw(N) * elt_ws(fn->opt.dtype);
+  }
+  return (size_t)d.cg.ws_rows * round_up(N, 32) * elt_ws(fn->opt.dtype);
+}
+
+bool all_bcast(const Graph& g, int64_t rows) {
+  for (int64_t r = 0; r < rows; ++r)
+    if (r >= (int64_t)g.in_bcast.size() || !g.in_bcast[r]) return false;
+  return true;
+}
+
+cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const void* X,
+                  int64_t ldx, const void* X2, int64_t ldx2, void* Y, int64_t ldy, int64_t N,
+                  void* W, int acc, int reduce, cusadi_stream stream) {
+  if (fn->path == CUSADI_PATH_INTERP) {
+    int rc = launch_interp((const IOp*)(adjoint ? ds.d_ops_adj : ds.d_ops_fwd),
+                           (int64_t)d.ip.ops.size(), adjoint ? ds.d_k_adj : ds.d_k_fwd,
+                           fn->opt.dtype, X, ldx, X2 ? X2 : X, ldx2, adjoint ? fn->ir.nnz_in : (int64_t)1 << 40,
+                           Y, ldy, N, W, interp_ldw(N), d.ip.n_slots, acc, reduce, stream);
+    if (rc != 0) return fail(CUSADI_E_CUDA, std::string("interpreter launch: ") + cudaGetErrorString((cudaError_t)rc));
+    return CUSADI_OK;
+  }
+  const std::vector<CUfunction>& fs = adjoint ? ds.adj : ds.fwd;
+  const unsigned block = (unsigned)fn->opt.block;
+  const unsigned grid = (unsigned)((N + block - 1) / block);
+  long long lx = ldx, lx2 = ldx2, ly = ldy, n = N, lw = round_up(N, 32);
+  const void* x2 = X2 ? X2 : X;
+  for (size_t s = 0; s < fs.size(); ++s) {
+    void* args[] = {(void*)&X, &lx, (void*)&x2, &lx2, &Y, &ly, &n, &W, &lw, &acc, &reduce};
+    CUresult r = driver().launchKernel(fs[s], grid, 1, 1, block, 1, 1, 0, (CUstream)stream, args, nullptr);
+    if (r != CUDA_SUCCESS) return cuda_fail("cuLaunchKernel", r);
+  }
+  return CUSADI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cusadi_default_options(cusadi_options* o) {
+  if (!o) return;
+  o->dtype = CUSADI_F64;
+  o->path = CUSADI_PATH_AUTO;
+  o->compile_limit_ops = 300000;
+  o->segment_ops = 40000;
+  o->block = 128;
+  o->maxrregcount = 0;
+  o->fmad = 1;
+  o->compile_threads = 0;
+  o->schedule = 1;
+  o->inline_math = 0;
+  o->adjoint = 0;
+  o->cache_dir = nullptr;
+}
+
+const char* cusadi_status_string(cusadi_status s) {
+  switch (s) {
+    case CUSADI_OK: return "ok";
+    case CUSADI_E_INVALID_ARG: return "invalid argument";
+    case CUSADI_E_INVALID_IR: return "invalid program";
+    case CUSADI_E_COMPILE: return "compilation failed";
+    case CUSADI_E_CUDA: return "CUDA error";
+    case CUSADI_E_OOM: return "out of host memory";
+    case CUSADI_E_TIMEOUT: return "timeout";
+    case CUSADI_E_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* cusadi_last_error(void) { return t_last_error.c_str(); }
+
+cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* opt,
+                          cusadi_fn* out) {
+  if (!out) return fail(CUSADI_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ir || nbytes == 0) return fail(CUSADI_E_INVALID_ARG, "empty program");
+  std::unique_ptr<cusadi_fn_s> fn;
+  try {
+    fn.reset(new cusadi_fn_s);
+  } catch (...) {
+    return fail(CUSADI_E_OOM, "allocation failed");
+  }
+  cusadi_default_options(&fn->opt);
+  if (opt) fn->opt = *opt;
+  cusadi_options& o = fn->opt;
+  if (o.dtype < 0 || o.dtype > 2) return fail(CUSADI_E_INVALID_ARG, "dtype must be F64, F32 or MIXED");
+  if (o.path < 0 || o.path > 2) return fail(CUSADI_E_INVALID_ARG, "unknown path");
+  if (o.block <= 0) o.block = 128;
+  if (o.block % 32 != 0 || o.block > 1024) return fail(CUSADI_E_INVALID_ARG, "block must be a multiple of 32 in [32, 1024]");
+  if (o.maxrregcount < 0 || o.maxrregcount > 255) return fail(CUSADI_E_INVALID_ARG, "maxrregcount must be in [0, 255]");
+  if (o.compile_limit_ops <= 0) o.compile_limit_ops = 300000;
+  if (o.cache_dir) fn->cache_dir = o.cache_dir;
+  o.cache_dir = nullptr;  // the caller's string is not kept
+  auto t0 = std::chrono::steady_clock::now();
+  try {
+    std::string err;
+    if (!parse_ir((const uint8_t*)ir, nbytes, fn->ir, err)) return fail(CUSADI_E_INVALID_IR, err);
+    fn->fwd.g = build_ssa(fn->ir);
+    // decide the path on the simplified size
+    Graph probe = fn->fwd.g;
+    simplify(probe, o.dtype);
+    int64_t ops = count_ops(probe);
+    if (o.path == CUSADI_PATH_INTERP || (o.path == CUSADI_PATH_AUTO && ops > o.compile_limit_ops))
+      fn->path = CUSADI_PATH_INTERP;
+    else
+      fn->path = CUSADI_PATH_COMPILED;
+    cusadi_status s = prepare_direction(fn.get(), fn->fwd, false);
+    if (s != CUSADI_OK) return s;
+    fn->compile_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (o.adjoint) {
+      s = ensure_adjoint(fn.get());
+      if (s != CUSADI_OK) return s;
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(CUSADI_E_OOM, "out of host memory during load");
+  }
+  *out = fn.release();
+  return CUSADI_OK;
+}
+
+void cusadi_free(cusadi_fn fn) {
+  if (!fn) return;
+  for (auto& kv : fn->dev) {
+    DevState& ds = kv.second;
+    if (cudaSetDevice(kv.first) == cudaSuccess) {
+      for (CUmodule m : ds.mods) if (driver().ok) driver().moduleUnload(m);
+      if (ds.d_ops_fwd) cudaFree(ds.d_ops_fwd);
+      if (ds.d_k_fwd) cudaFree(ds.d_k_fwd);
+      if (ds.d_ops_adj) cudaFree(ds.d_ops_adj);
+      if (ds.d_k_adj) cudaFree(ds.d_k_adj);
+    }
+  }
+  delete fn;
+}
+
+cusadi_status cusadi_info(cusadi_fn fn, cusadi_fn_info* o) {
+  if (!fn || !o) return fail(CUSADI_E_INVALID_ARG, "NULL argument");
+  std::memset(o, 0, sizeof *o);
+  o->n_in = (int32_t)fn->ir.in.size();
+  o->n_out = (int32_t)fn->ir.out.size();
+  o->nnz_in = fn->ir.nnz_in;
+  o->nnz_out = fn->ir.nnz_out;
+  o->n_instr = (int64_t)fn->ir.code.size();
+  o->n_work = fn->ir.n_work;
+  o->n_ops_ir = fn->ir.n_ops;
+  o->n_ops = fn->fwd.n_ops;
+  o->n_slots = fn->fwd.n_slots;
+  o->path = fn->path;
+  o->n_segments = fn->path == CUSADI_PATH_COMPILED ? (int32_t)fn->fwd.cg.segs.size() : 0;
+  o->dtype = fn->opt.dtype;
+  int32_t nb = 0;
+  for (uint8_t b : fn->fwd.g.in_bcast) nb += b;
+  o->n_bcast_in = nb;
+  o->compile_seconds = fn->compile_seconds;
+  return CUSADI_OK;
+}
+
+cusadi_status cusadi_arg_info(cusadi_fn fn, int is_output, int index, cusadi_arg* out) {
+  if (!fn || !out) return fail(CUSADI_E_INVALID_ARG, "NULL argument");
+  const std::vector<Arg>& v = is_output ? fn->ir.out : fn->ir.in;
+  if (index < 0 || index >= (int)v.size()) return fail(CUSADI_E_INVALID_ARG, "argument index out of range");
+  const Arg& a = v[index];
+  out->nrow = a.nrow;
+  out->ncol = a.ncol;
+  out->nnz = a.nnz;
+  out->flags = a.flags;
+  out->row_offset = a.offset;
+  out->rowptr = a.rowptr.data();
+  out->col = a.col.data();
+  out->name = a.name.c_str();
+  return CUSADI_OK;
+}
+
+cusadi_status cusadi_op_counts(cusadi_fn fn, int adjoint, int64_t* counts, int n) {
+  if (!fn || !counts || n < 0) return fail(CUSADI_E_INVALID_ARG, "NULL argument");
+  if (adjoint) {
+    cusadi_status s = ensure_adjoint(fn);
+    if (s != CUSADI_OK) return s;
+  }
+  const std::vector<int64_t>& h = adjoint ? fn->adj.hist : fn->fwd.hist;
+  for (int i = 0; i < n; ++i) counts[i] = i < (int)h.size() ? h[i] : 0;
+  return CUSADI_OK;
+}
+
+size_t cusadi_workspace_bytes(cusadi_fn fn, int64_t N, int adjoint) {
+  if (!fn || N <= 0) return 0;
+  if (adjoint) {
+    if (ensure_adjoint(fn) != CUSADI_OK) return 0;
+    return direction_ws(fn, fn->adj, N);
+  }
+  return direction_ws(fn, fn->fwd, N);
+}
+
+cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out, int64_t ld_out,
+                          int64_t N, void* workspace, cusadi_stream stream) {
+  if (!fn) return fail(CUSADI_E_INVALID_ARG, "fn is NULL");
+  if (N < 0) return fail(CUSADI_E_INVALID_ARG, "N must be >= 0");
+  if (N == 0) return CUSADI_OK;
+  if (N > ((int64_t)1 << 40)) return fail(CUSADI_E_INVALID_ARG, "N too large");
+  if (fn->ir.nnz_in > 0) {
+    if (!in) return fail(CUSADI_E_INVALID_ARG, "in is NULL");
+    int64_t need = all_bcast(fn->fwd.g, fn->ir.nnz_in) ? 1 : N;
+    if (ld_in < need) return fail(CUSADI_E_INVALID_ARG, "ld_in smaller than N");
+  }
+  if (fn->ir.nnz_out > 0) {
+    if (!out) return fail(CUSADI_E_INVALID_ARG, "out is NULL");
+    if (ld_out < N) return fail(CUSADI_E_INVALID_ARG, "ld_out smaller than N");
+  } else {
+    return CUSADI_OK;
+  }
+  if (direction_ws(fn, fn->fwd, N) > 0 && !workspace)
+    return fail(CUSADI_E_INVALID_ARG, "this function needs a workspace (cusadi_workspace_bytes)");
+  DevState* ds;
+  cusadi_status s = device_state(fn, false, &ds);
+  if (s != CUSADI_OK) return s;
+  return run(fn, fn->fwd, *ds, false, in, ld_in, nullptr, 0, out, ld_out, N, workspace, 0, 0, stream);
+}
+
+cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,
+                             int64_t ld_ob, void* in_bar, int64_t ld_ib, int64_t N,
+                             uint32_t flags, void* workspace, cusadi_stream stream) {
+  if (!fn) return fail(CUSADI_E_INVALID_ARG, "fn is NULL");
+  if (N < 0) return fail(CUSADI_E_INVALID_ARG, "N must be >= 0");
+  if (flags & ~(CUSADI_ADJ_ACCUMULATE | CUSADI_ADJ_REDUCE_BROADCAST))
+    return fail(CUSADI_E_INVALID_ARG, "unknown adjoint flags");
+  cusadi_status s = ensure_adjoint(fn);
+  if (s != CUSADI_OK) return s;
+  if (N == 0 || fn->ir.nnz_in == 0) return CUSADI_OK;
+  if (!in || !in_bar) return fail(CUSADI_E_INVALID_ARG, "in / in_bar is NULL");
+  const bool reduce = (flags & CUSADI_ADJ_REDUCE_BROADCAST) != 0;
+  int64_t need = all_bcast(fn->fwd.g, fn->ir.nnz_in) ? 1 : N;
+  if (ld_in < need) return fail(CUSADI_E_INVALID_ARG, "ld_in smaller than N");
+  if (fn->ir.nnz_out > 0 && (!out_bar || ld_ob < N)) return fail(CUSADI_E_INVALID_ARG, "out_bar missing or ld_ob smaller than N");
+  if (ld_ib < (reduce && all_bcast(fn->fwd.g, fn->ir.nnz_in) ? 1 : N)) return fail(CUSADI_E_INVALID_ARG, "ld_ib smaller than N");
+  if (direction_ws(fn, fn->adj, N) > 0 && !workspace)
+    return fail(CUSADI_E_INVALID_ARG, "this function needs a workspace (cusadi_workspace_bytes)");
+  DevState* ds;
+  s = device_state(fn, true, &ds);
+  if (s != CUSADI_OK) return s;
+  const int acc = (flags & CUSADI_ADJ_ACCUMULATE) ? 1 : 0;
+  const bool has_reduce = fn->path == CUSADI_PATH_INTERP ? fn->adj.ip.has_reduce : fn->adj.cg.has_reduce;
+  if (reduce && !acc && has_reduce) {
+    if (fn->path == CUSADI_PATH_INTERP) {
+      // clear column 0 of the broadcast rows
+      const size_t e = elt_io(fn->opt.dtype);
+      for (int64_t r = 0; r < fn->ir.nnz_in; ++r) {
+        if (!fn->fwd.g.in_bcast[r]) continue;
+        cudaError_t ce = cudaMemsetAsync((char*)in_bar + (size_t)r * ld_ib * e, 0, e, (cudaStream_t)stream);
+        if (ce != cudaSuccess) return cuda_fail("cudaMemsetAsync", ce);
+      }
+    } else {
+      long long ly = ld_ib;
+      void* args[] = {&in_bar, &ly};
+      CUresult r = driver().launchKernel(ds->adj_zero, 1, 1, 1, 32, 1, 1, 0, (CUstream)stream, args, nullptr);
+      if (r != CUDA_SUCCESS) return cuda_fail("cuLaunchKernel", r);
+    }
+  }
+  return run(fn, fn->adj, *ds, true, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, workspace, acc,
+             reduce ? 1 : 0, stream);
+}
+
+cusadi_status cusadi_source(cusadi_fn fn, int adjoint, int segment, char* buf, size_t* len) {
+  if (!fn || !len) return fail(CUSADI_E_INVALID_ARG, "NULL argument");
+  if (fn->path != CUSADI_PATH_COMPILED) return fail(CUSADI_E_UNSUPPORTED, "interpreted function has no source");
+  if (adjoint) {
+    cusadi_status s = ensure_adjoint(fn);
+    if (s != CUSADI_OK) return s;
+  }
+  const Direction& d = adjoint ? fn->adj : fn->fwd;
+  if (segment < 0 || segment >= (int)d.cg.segs.size()) return fail(CUSADI_E_INVALID_ARG, "segment out of range");
+  const std::string& src = d.cg.segs[segment].source;
+  if (buf && *len > 0) {
+    size_t n = std::min(*len - 1, src.size());
+    std::memcpy(buf, src.data(), n);
+    buf[n] = 0;
+  }
+  *len = src.size() + 1;
+  return CUSADI_OK;
+}
+
+}  // extern "C"

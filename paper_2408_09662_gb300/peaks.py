@@ -1,0 +1,115 @@
+"""Measured arithmetic peaks and per-op costs for the ALU roofline.
+
+A straight-line program is bound by the FP32 or FP64 pipes, not by memory, so
+its roofline is an op rate.  Each op is timed here as long independent chains
+(8 per thread, enough threads to fill every SM) through the engine's own
+compiled kernels, against the same chains of fused multiply-adds:
+
+    peak     = FMA chains' rate (FMA/s)              - the denominator
+    w(op)    = time per op / time per FMA            - FMA-equivalent cost
+
+so ``sum_op w(op) * count(op) * N / time`` over ``peak`` is the fraction of
+the measured FMA rate a kernel reaches.  Chains that need a helper op to stay
+bounded (exp, log) have the helper's cost subtracted.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import tracer as T
+from .api import Function
+from .ir import Op
+
+CHAINS = 8
+LENGTH = {"fma": 256, "add": 256, "mul": 256, "div": 64, "sqrt": 64, "sin": 16, "cos": 16,
+          "exp_mul": 16, "log_add": 16}
+
+
+def _chain_program(kind: str):
+    """CHAINS independent chains of LENGTH[kind] steps, interleaved step by step."""
+    g = T.Graph()
+    v = g.symbols(CHAINS)
+    w = g.symbols(CHAINS)
+    xs = list(v)
+    for _ in range(LENGTH[kind]):
+        for c in range(CHAINS):
+            x, y = xs[c], w[c]
+            if kind == "fma":
+                x = T.fma_const(0.999, x, y)
+            elif kind == "add":
+                x = x + y
+            elif kind == "mul":
+                x = x * 0.9999
+            elif kind == "div":
+                x = y / x
+            elif kind == "sqrt":
+                x = T.sqrt(x)
+            elif kind == "sin":
+                x = T.sin(x)
+            elif kind == "cos":
+                x = T.cos(x)
+            elif kind == "exp_mul":
+                x = T.exp(x) * 0.1
+            elif kind == "log_add":
+                x = T.log(x) + y
+            xs[c] = x
+    return T.Function([("v", v), ("w", w)], [("y", xs)]).to_ir()
+
+
+# op -> (chain kind, helper op whose cost is subtracted)
+OP_CHAINS = {Op.FMA_CONST: ("fma", None), Op.ADD: ("add", None), Op.SUB: ("add", None),
+             Op.MUL: ("mul", None), Op.SQ: ("mul", None), Op.DIV: ("div", None),
+             Op.SQRT: ("sqrt", None), Op.SIN: ("sin", None), Op.COS: ("cos", None),
+             Op.EXP: ("exp_mul", Op.MUL), Op.LOG: ("log_add", Op.ADD)}
+
+
+def _time(fn: Function, x: torch.Tensor, reps: int = 5) -> float:
+    y = fn(x)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn(x, out=y)
+        e.record()
+        e.synchronize()
+        best = min(best, s.elapsed_time(e) * 1e-3)
+    return best
+
+
+def measure(dtype: str, n_instances: int | None = None) -> dict:
+    """{"fma_per_s": peak, "weights": {op name: w}} for "f64" or "f32"."""
+    props = torch.cuda.get_device_properties(0)
+    N = n_instances or props.multi_processor_count * 2048 * 2
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    rng = np.random.default_rng(0)
+    x = torch.tensor(np.vstack([rng.uniform(0.5, 1.5, (CHAINS, N)),
+                                rng.uniform(1.0, 2.0, (CHAINS, N))]), dtype=tdt, device="cuda")
+    from concurrent.futures import ThreadPoolExecutor
+    kinds = sorted({k for k, _ in OP_CHAINS.values()})
+    # math is inlined here: the weights describe the ops, not the call overhead
+    with ThreadPoolExecutor(len(kinds)) as ex:
+        fns = dict(zip(kinds, ex.map(lambda k: Function(_chain_program(k), dtype=dtype, schedule=0,
+                                                         inline_math=1), kinds)))
+    times = {k: _time(fns[k], x) / (fns[k].info.n_ops * N) for k in kinds}
+    t_fma = times["fma"]
+    per_op = {}
+    for op, (kind, helper) in OP_CHAINS.items():
+        t = times[kind]
+        if helper is not None:
+            # the chain alternates op and helper: per pair = 2 * t
+            t = max(2 * t - times[OP_CHAINS[helper][0]], 0.0)
+        per_op[op.name] = t / t_fma
+    per_op["NEG"] = 0.0   # folded into the consumer as an operand modifier
+    return {"fma_per_s": 1.0 / t_fma, "weights": per_op, "instances": N}
+
+
+def weighted_ops(counts, weights: dict) -> float:
+    """FMA-equivalent work per instance; ops without a measured weight count 1."""
+    total = 0.0
+    for op in Op:
+        c = counts[int(op)] if int(op) < len(counts) else 0
+        if c:
+            total += c * weights.get(op.name, 1.0)
+    return total

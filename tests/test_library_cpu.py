@@ -1,0 +1,209 @@
+"""Host-side tests of libcusadi (no GPU): the library loads, exports every
+entry point of include/cusadi.h, validates programs, runs its passes and
+generates + compiles code with NVRTC."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2408_09662_gb300 import _lib as L
+from paper_2408_09662_gb300 import programs
+from paper_2408_09662_gb300.ir import Instr, Op, ProgramIR, Sparsity
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "cusadi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cusadi_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point():
+    names = _declared_functions()
+    assert "cusadi_load" in names and "cusadi_eval" in names and "cusadi_adjoint" in names
+    lib = L.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(L.SIGNATURES)
+
+
+def test_default_options():
+    o = L.cusadi_default_options()
+    assert (o.dtype, o.path, o.block, o.fmad, o.schedule) == (0, 0, 128, 1, 1)
+
+
+def _opt(**kw):
+    o = L.cusadi_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def test_load_info_and_arg_patterns():
+    fn = L.cusadi_load(programs.cartpole_rk4().to_bytes(), _opt())
+    try:
+        i = L.cusadi_info(fn)
+        assert (i.n_in, i.n_out, i.nnz_in, i.nnz_out) == (2, 2, 5, 24)
+        assert i.path == L.CUSADI_PATH_COMPILED and i.n_segments == 1
+        assert 0 < i.n_ops <= i.n_ops_ir
+        jac = L.cusadi_arg_info(fn, True, 1)
+        assert (jac.nrow, jac.ncol, jac.nnz, jac.row_offset) == (4, 5, 20, 4)
+        assert [jac.rowptr[k] for k in range(5)] == [0, 5, 10, 15, 20]
+        assert [jac.col[k] for k in range(5)] == [0, 1, 2, 3, 4]
+        assert jac.name == b"jac"
+        counts = L.cusadi_op_counts(fn)
+        assert sum(counts) == i.n_ops
+        assert counts[Op.SIN] > 0 and counts[Op.COS] > 0
+    finally:
+        L.cusadi_free(fn)
+
+
+def test_generated_source_follows_listing2():
+    fn = L.cusadi_load(programs.listing2().to_bytes(), _opt())
+    src = L.cusadi_source(fn)
+    L.cusadi_free(fn)
+    body = [l.strip() for l in src.splitlines() if l.strip().startswith(("const double v", "Y["))]
+    assert body == ["const double v0 = (double)X[0ll * ldx];",
+                    "const double v1 = cs_sin_d(v0);",
+                    "const double v2 = v0 + v1;",
+                    "const double v3 = v2 * v2;",
+                    "Y[0ll * ldy] = (double)v3;"]
+
+
+def test_fp32_source_uses_float_math_and_literals():
+    fn = L.cusadi_load(programs.random_program(200, n_in=4, n_out=2, seed=3).to_bytes(),
+                       _opt(dtype=L.CUSADI_F32))
+    src = L.cusadi_source(fn)
+    L.cusadi_free(fn)
+    assert "double" not in src
+    assert re.search(r"fmaf\(\(0x[0-9a-f.]+p[-+]\d+f\)", src)
+
+
+@pytest.mark.parametrize("mutate,what", [
+    (lambda b: b"XXXX" + b[4:], "magic"),
+    (lambda b: b[:-3], "truncated"),
+    (lambda b: b + b"\0", "trailing"),
+])
+def test_malformed_bytes_are_rejected(mutate, what):
+    with pytest.raises(L.CusadiError) as e:
+        L.cusadi_load(mutate(programs.listing2().to_bytes()))
+    assert e.value.status == L.CUSADI_E_INVALID_IR
+
+
+def _listing2_with(instrs, n_work=2):
+    return ProgramIR(n_work, [Sparsity.dense(1, 1, "x")], [Sparsity.dense(1, 1, "y")], instrs, [])
+
+
+@pytest.mark.parametrize("instrs,msg", [
+    ([Instr(Op.INPUT, 0, 0), Instr(Op.SIN, 1, 5), Instr(Op.OUTPUT, 0, 1)], "undefined"),
+    ([Instr(Op.INPUT, 0, 0), Instr(Op.SIN, 1, 1), Instr(Op.OUTPUT, 0, 1)], "undefined"),
+    ([Instr(Op.INPUT, 0, 3), Instr(Op.OUTPUT, 0, 0)], "input row"),
+    ([Instr(Op.INPUT, 0, 0)], "written 0 times"),
+    ([Instr(Op.INPUT, 0, 0), Instr(Op.OUTPUT, 0, 0), Instr(Op.OUTPUT, 0, 0)], "written 2 times"),
+    ([Instr(Op.INPUT, 0, 0), Instr(99, 1, 0), Instr(Op.OUTPUT, 0, 1)], "unknown op"),
+    ([Instr(Op.INPUT, 0, 0), Instr(Op.CONST, 1, 4), Instr(Op.OUTPUT, 0, 1)], "constant"),
+])
+def test_inconsistent_programs_are_rejected(instrs, msg):
+    with pytest.raises(L.CusadiError) as e:
+        L.cusadi_load(_listing2_with(instrs).to_bytes())
+    assert e.value.status == L.CUSADI_E_INVALID_IR
+    assert msg in str(e.value)
+
+
+def test_bad_sparsity_is_rejected():
+    ir = programs.listing2()
+    ir.outputs = [Sparsity(1, 1, [0, 2], [0, 0], "y")]
+    with pytest.raises(L.CusadiError):
+        L.cusadi_load(ir.to_bytes())
+
+
+@pytest.mark.parametrize("field,value", [("dtype", 7), ("block", 100), ("block", 2048),
+                                         ("maxrregcount", 300), ("path", 9)])
+def test_bad_options_are_rejected(field, value):
+    with pytest.raises(L.CusadiError) as e:
+        L.cusadi_load(programs.listing2().to_bytes(), _opt(**{field: value}))
+    assert e.value.status == L.CUSADI_E_INVALID_ARG
+
+
+def test_eval_argument_errors_are_caught_on_the_host():
+    fn = L.cusadi_load(programs.listing2().to_bytes(), _opt())
+    try:
+        L.cusadi_eval(fn, 0, 0, 0, 0, 0, 0, 0)        # N = 0 is a no-op
+        with pytest.raises(L.CusadiError):
+            L.cusadi_eval(fn, 0, 16, 0, 16, -1, 0, 0)  # N < 0
+        with pytest.raises(L.CusadiError):
+            L.cusadi_eval(fn, 0, 16, 8, 16, 16, 0, 0)  # NULL input
+        with pytest.raises(L.CusadiError):
+            L.cusadi_eval(fn, 8, 8, 8, 16, 16, 0, 0)   # ld_in < N
+        with pytest.raises(L.CusadiError):
+            L.cusadi_adjoint(fn, 8, 16, 8, 16, 8, 16, 16, 8, 0, 0)  # unknown flag
+    finally:
+        L.cusadi_free(fn)
+
+
+def test_segmented_program_needs_a_workspace():
+    ir = programs.random_program(3000, n_in=16, n_out=8, seed=5).to_bytes()
+    fn = L.cusadi_load(ir, _opt(segment_ops=700, dtype=L.CUSADI_F32))
+    try:
+        i = L.cusadi_info(fn)
+        assert i.n_segments >= 3
+        nb = L.cusadi_workspace_bytes(fn, 1000, False)
+        assert nb > 0 and nb % (4 * 1024) == 0        # rows x round_up(N, 32) floats
+        with pytest.raises(L.CusadiError):
+            L.cusadi_eval(fn, 8, 1000, 8, 1000, 1000, 0, 0)
+    finally:
+        L.cusadi_free(fn)
+
+
+def test_interpreter_path_packs_without_compiling():
+    ir = programs.random_program(5000, seed=7).to_bytes()
+    fn = L.cusadi_load(ir, _opt(path=L.CUSADI_PATH_INTERP))
+    try:
+        i = L.cusadi_info(fn)
+        assert i.path == L.CUSADI_PATH_INTERP and i.n_segments == 0
+        assert i.compile_seconds < 5
+        with pytest.raises(L.CusadiError) as e:
+            L.cusadi_source(fn)
+        assert e.value.status == L.CUSADI_E_UNSUPPORTED
+    finally:
+        L.cusadi_free(fn)
+
+
+def test_auto_path_respects_compile_limit():
+    ir = programs.random_program(800, seed=8).to_bytes()
+    fn = L.cusadi_load(ir, _opt(compile_limit_ops=100))
+    assert L.cusadi_info(fn).path == L.CUSADI_PATH_INTERP
+    L.cusadi_free(fn)
+
+
+def test_scheduling_lowers_live_values():
+    ir = programs.random_program(5000, seed=9).to_bytes()
+    a = L.cusadi_load(ir, _opt(path=L.CUSADI_PATH_INTERP, schedule=0))
+    b = L.cusadi_load(ir, _opt(path=L.CUSADI_PATH_INTERP, schedule=1))
+    sa, sb = L.cusadi_info(a).n_slots, L.cusadi_info(b).n_slots
+    L.cusadi_free(a)
+    L.cusadi_free(b)
+    assert sb < sa
+
+
+def test_adjoint_source_generates_reduction_for_broadcast_inputs():
+    from paper_2408_09662_gb300 import tracer as T
+    from paper_2408_09662_gb300.ir import ARG_BROADCAST
+    g = T.Graph()
+    x = g.symbols(2)
+    k = g.symbols(2)
+    y = [T.sin(x[0]) * k[0] + x[1] * k[1]]
+    ir = T.Function([("x", x), ("k", k, ARG_BROADCAST)], [("y", y)]).to_ir()
+    fn = L.cusadi_load(ir.to_bytes(), _opt())
+    try:
+        src = L.cusadi_source(fn, adjoint=True)
+        assert "__shfl_xor_sync" in src and "atomicAdd(&Yb[2ll * ldy]" in src
+        assert "atomicAdd(&Yb[3ll * ldy]" in src and "cs_adj_zero" in src
+        assert L.cusadi_info(fn).n_bcast_in == 2
+        counts = L.cusadi_op_counts(fn, adjoint=True)
+        assert counts[Op.COS] == 1
+    finally:
+        L.cusadi_free(fn)
