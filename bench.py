@@ -155,6 +155,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="reuse peaks measured earlier on this machine (_build/peaks.json)")
+    ap.add_argument("--only", choices=["both", "f64", "f32"], default="both",
+                    help="time one kernel only (for profiling); prints no JSON line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -209,6 +213,13 @@ def main():
         fn64(x64, out=y64)
         fn32(x32, out=y32)
     torch.cuda.synchronize()
+    if args.only != "both":
+        fn, x, y = (fn64, x64, y64) if args.only == "f64" else (fn32, x32, y32)
+        ev = timed(fn, x, y, args.steps)
+        torch.cuda.synchronize()
+        ms = sum(s.elapsed_time(e) for s, e in ev) / args.steps
+        print(f"{args.only}: {ms:.4f} ms/step over {args.steps} steps", flush=True)
+        return
 
     # ---- timed region: K FP64 steps ------------------------------------------
     if world > 1:
@@ -273,7 +284,7 @@ def main():
     rel64 = np.abs(y64.cpu().numpy()[:, idx] - ref64) / np.max(np.abs(ref64), axis=1, keepdims=True)
 
     # ---- roofline: measured FMA rate and per-op weights -------------------------
-    pk64, pk32 = peaks.measure("f64"), peaks.measure("f32")
+    pk64, pk32 = peaks.cached_or_measure(torch.cuda.get_device_name(dev), reuse=args.no_peaks)
     w64 = peaks.weighted_ops(fn64.op_counts(), pk64["weights"])
     w32 = peaks.weighted_ops(fn32.op_counts(), pk32["weights"])
     t64, t32 = ms_per_step * 1e-3, ms32 * 1e-3

@@ -127,4 +127,6 @@ def tolerance(oracle: Oracle, x, y_ref, tau: float, kind: int, kappa: float = 2.
     B = oracle.rounding_bound(x, kind=kind)
     if kind == 1:
         B = B + np.ldexp(1.0, -24) * np.abs(y_ref)
-    return np.maximum(tau * s, kappa * B)
+    # where the bound is undefined (a derivative blows up at a discontinuity of
+    # the program) only the stated relative tolerance applies
+    return np.fmax(tau * s, kappa * B)

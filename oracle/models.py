@@ -98,3 +98,106 @@ def rk4_linear_maps(A, B, dt):
 # ---------------------------------------------------------------------------
 def pendulum_energy(th, om, g_over_l=9.81):
     return 0.5 * np.asarray(om) ** 2 - g_over_l * np.cos(th)
+
+
+# ---------------------------------------------------------------------------
+# closed-form MPC of the planar quadrotor (barrier Newton, M fixed iterations)
+# restated densely: z = (x_0..x_T, u_0..u_{T-1}), KKT solved by LAPACK
+# ---------------------------------------------------------------------------
+QUAD = dict(mass=1.0, inertia=0.01, arm=0.2, g=9.81, dt=0.02, T=10,
+            q=(10.0, 10.0, 1.0, 1.0, 1.0, 1.0), r=0.1, u_max=15.0, mu0=0.1, mu_end=0.001,
+            M=5, delta=1e-9, tau=0.995)
+
+
+def quad_step(x, u, p):
+    px, pz, th, vx, vz, om = x
+    F = u[0] + u[1]
+    vx1 = vx + p["dt"] * (-F * math.sin(th) / p["mass"])
+    vz1 = vz + p["dt"] * (F * math.cos(th) / p["mass"] - p["g"])
+    om1 = om + p["dt"] * (p["arm"] * (u[0] - u[1]) / p["inertia"])
+    return np.array([px + p["dt"] * vx1, pz + p["dt"] * vz1, th + p["dt"] * om1, vx1, vz1, om1])
+
+
+def quad_step_jac(x, u, p):
+    """(A, B) = d step / d x, d step / d u, by hand."""
+    th = x[2]
+    F = u[0] + u[1]
+    dt, m = p["dt"], p["mass"]
+    s, c = math.sin(th), math.cos(th)
+    B = np.zeros((6, 2))
+    B[3, :] = -dt * s / m
+    B[4, :] = dt * c / m
+    B[5, :] = [dt * p["arm"] / p["inertia"], -dt * p["arm"] / p["inertia"]]
+    B[0:3, :] = dt * B[3:6, :]
+    A = np.eye(6)
+    A[3, 2] = -dt * F * c / m
+    A[4, 2] = -dt * F * s / m
+    A[0, 3] = A[1, 4] = A[2, 5] = dt
+    A[0, 2] = dt * A[3, 2]
+    A[1, 2] = dt * A[4, 2]
+    return A, B
+
+
+def quad_kkt(x, u, x0bar, wp, mu, p):
+    """KKT matrix and right-hand side at (x, u): unknowns (dz, lambda)."""
+    Tn = p["T"]
+    nx, nu = 6 * (Tn + 1), 2 * Tn
+    nz, nl = nx + nu, 6 * (Tn + 1)
+    Q = np.diag(p["q"])
+    xref = np.array([wp[0], wp[1], 0, 0, 0, 0.0])
+    uh = p["mass"] * p["g"] / 2
+    H = np.zeros((nz, nz))
+    g = np.zeros(nz)
+    for k in range(Tn + 1):
+        H[6 * k:6 * k + 6, 6 * k:6 * k + 6] = 2 * Q
+        g[6 * k:6 * k + 6] = 2 * Q @ (x[k] - xref)
+    for k in range(Tn):
+        for j in range(2):
+            a = nx + 2 * k + j
+            lo, hi = 1 / u[k][j], 1 / (p["u_max"] - u[k][j])
+            H[a, a] = 2 * p["r"] + mu * (lo * lo + hi * hi)
+            g[a] = 2 * p["r"] * (u[k][j] - uh) - mu * (lo - hi)
+    A = np.zeros((nl, nz))
+    c = np.zeros(nl)
+    A[0:6, 0:6] = np.eye(6)
+    c[0:6] = x[0] - x0bar
+    for k in range(Tn):
+        Ak, Bk = quad_step_jac(x[k], u[k], p)
+        r = 6 * (k + 1)
+        A[r:r + 6, 6 * (k + 1):6 * (k + 2)] = np.eye(6)
+        A[r:r + 6, 6 * k:6 * k + 6] = -Ak
+        A[r:r + 6, nx + 2 * k:nx + 2 * k + 2] = -Bk
+        c[r:r + 6] = x[k + 1] - quad_step(x[k], u[k], p)
+    K = np.block([[H, A.T], [A, -p["delta"] * np.eye(nl)]])
+    rhs = np.concatenate([-g, -c])
+    return K, rhs
+
+
+def quadrotor_mpc(x0bar, wp, M=None, **over):
+    """z after M barrier-Newton iterations (the reading documented with the
+    program generator), with every KKT system solved densely by LAPACK."""
+    p = dict(QUAD)
+    p.update(over)
+    if M is not None:
+        p["M"] = M
+    Tn = p["T"]
+    uh = p["mass"] * p["g"] / 2
+    u = [np.array([uh, uh]) for _ in range(Tn)]
+    x = [np.asarray(x0bar, dtype=np.float64)]
+    for k in range(Tn):
+        x.append(quad_step(x[k], u[k], p))
+    nx = 6 * (Tn + 1)
+    for it in range(p["M"]):
+        mu = p["mu0"] * (p["mu_end"] / p["mu0"]) ** (it / (p["M"] - 1)) if p["M"] > 1 else p["mu0"]
+        K, rhs = quad_kkt(x, u, x0bar, wp, mu, p)
+        s = np.linalg.solve(K, rhs)
+        du = s[nx:nx + 2 * Tn].reshape(Tn, 2)
+        dx = s[:nx].reshape(Tn + 1, 6)
+        U = np.array(u)
+        with np.errstate(divide="ignore"):
+            lo = np.where(du < 0, U / np.maximum(-du, 0), np.inf)
+            hi = np.where(du > 0, (p["u_max"] - U) / np.maximum(du, 0), np.inf)
+        alpha = min(1.0, p["tau"] * float(np.min(np.minimum(lo, hi))))
+        x = [x[k] + alpha * dx[k] for k in range(Tn + 1)]
+        u = [u[k] + alpha * du[k] for k in range(Tn)]
+    return np.concatenate([np.concatenate(x), np.concatenate(u)])

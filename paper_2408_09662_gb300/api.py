@@ -92,6 +92,11 @@ class Function:
             self._ws[key] = ws
         return ws
 
+    @staticmethod
+    def _ld(t: torch.Tensor) -> int:
+        # a single row's stride is meaningless (torch may report anything); use N
+        return t.stride(0) if t.shape[0] > 1 else max(t.shape[1], 1)
+
     def _check(self, t: torch.Tensor, rows: int, name: str):
         if not t.is_cuda:
             raise ValueError(f"{name} must be a CUDA tensor (data stays on the GPU)")
@@ -108,7 +113,7 @@ class Function:
             out = torch.empty((self.nnz_out, N), dtype=self.torch_dtype, device=x.device)
         self._check(out, self.nnz_out, "out")
         ws = self.workspace(N, False, x.device)
-        L.cusadi_eval(self._fn, x.data_ptr(), x.stride(0), out.data_ptr(), out.stride(0), N,
+        L.cusadi_eval(self._fn, x.data_ptr(), self._ld(x), out.data_ptr(), self._ld(out), N,
                       ws.data_ptr() if ws is not None else 0,
                       torch.cuda.current_stream(x.device).cuda_stream)
         return out
@@ -126,8 +131,8 @@ class Function:
         flags = (L.CUSADI_ADJ_ACCUMULATE if accumulate else 0) | \
                 (L.CUSADI_ADJ_REDUCE_BROADCAST if reduce_broadcast else 0)
         ws = self.workspace(N, True, x.device)
-        L.cusadi_adjoint(self._fn, x.data_ptr(), x.stride(0), ybar.data_ptr(), ybar.stride(0),
-                         out.data_ptr(), out.stride(0), N, flags,
+        L.cusadi_adjoint(self._fn, x.data_ptr(), self._ld(x), ybar.data_ptr(), self._ld(ybar),
+                         out.data_ptr(), self._ld(out), N, flags,
                          ws.data_ptr() if ws is not None else 0,
                          torch.cuda.current_stream(x.device).cuda_stream)
         return out

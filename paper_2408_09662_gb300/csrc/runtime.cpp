@@ -200,7 +200,8 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.inline_math = fn->opt.inline_math != 0;
   co.adjoint = adjoint;
   co.split = adjoint ? fn->ir.nnz_in : -1;
-  co.prefix = adjoint ? "cs_adj" : "cs_fwd";
+  static const char* tag[] = {"f64", "f32", "mixed"};
+  co.prefix = std::string(adjoint ? "cs_adj_" : "cs_fwd_") + tag[fn->opt.dtype];
   d.cg = generate(d.g, co);
   const size_t ns = d.cg.segs.size();
   d.bins.assign(ns, std::string());

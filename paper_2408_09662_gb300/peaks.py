@@ -22,8 +22,8 @@ from .api import Function
 from .ir import Op
 
 CHAINS = 8
-LENGTH = {"fma": 256, "add": 256, "mul": 256, "div": 64, "sqrt": 64, "sin": 16, "cos": 16,
-          "exp_mul": 16, "log_add": 16}
+LENGTH = {"fma": 1024, "add": 1024, "mul": 1024, "div": 128, "sqrt": 128, "sin": 24, "cos": 24,
+          "exp_mul": 24, "log_add": 24}
 
 
 def _chain_program(kind: str):
@@ -81,7 +81,7 @@ def _time(fn: Function, x: torch.Tensor, reps: int = 5) -> float:
 def measure(dtype: str, n_instances: int | None = None) -> dict:
     """{"fma_per_s": peak, "weights": {op name: w}} for "f64" or "f32"."""
     props = torch.cuda.get_device_properties(0)
-    N = n_instances or props.multi_processor_count * 2048 * 2
+    N = n_instances or props.multi_processor_count * 2048 * 4
     tdt = torch.float64 if dtype == "f64" else torch.float32
     rng = np.random.default_rng(0)
     x = torch.tensor(np.vstack([rng.uniform(0.5, 1.5, (CHAINS, N)),
@@ -113,3 +113,21 @@ def weighted_ops(counts, weights: dict) -> float:
         if c:
             total += c * weights.get(op.name, 1.0)
     return total
+
+
+def cached_or_measure(gpu_name: str, reuse: bool, path: str | None = None):
+    """(f64, f32) peak records; measured now unless reuse and a record for this GPU exists."""
+    import json
+    import os
+    path = path or os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                "_build", "peaks.json")
+    if reuse and os.path.exists(path):
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("gpu") == gpu_name:
+            return rec["f64"], rec["f32"]
+    f64, f32 = measure("f64"), measure("f32")
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump({"gpu": gpu_name, "f64": f64, "f32": f32}, f)
+    return f64, f32

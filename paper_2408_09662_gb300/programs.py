@@ -174,3 +174,231 @@ def random_program(n_ops: int = 20000, n_in: int = 64, n_out: int = 32,
             v = T.fma_const(float(rng.uniform(-1.0, 1.0)), a, pick(vals))
         vals.append(v)
     return T.Function([("x", x)], [("y", vals[-n_out:])]).to_ir()
+
+
+# ---------------------------------------------------------------------------
+# Closed-form MPC: planar quadrotor, M unrolled barrier-Newton iterations
+# ---------------------------------------------------------------------------
+QUADROTOR = dict(mass=1.0, inertia=0.01, arm=0.2, g=9.81, dt=0.02, T=10,
+                 q=(10.0, 10.0, 1.0, 1.0, 1.0, 1.0), r=0.1, u_max=15.0, mu0=0.1, mu_end=0.001,
+                 M=5, delta=1e-9, tau=0.995)
+
+
+def quadrotor_step(x, u, p):
+    """Semi-implicit Euler step of the planar quadrotor (§V-C integrates its
+    quadcopter this way): x = [px, pz, th, vx, vz, om], u = [u1, u2] thrusts."""
+    px, pz, th, vx, vz, om = x
+    u1, u2 = u
+    thrust = u1 + u2
+    ax = -thrust * T.sin(th) / p["mass"]
+    az = thrust * T.cos(th) / p["mass"] - p["g"]
+    al = p["arm"] * (u1 - u2) / p["inertia"]
+    dt = p["dt"]
+    vx1, vz1, om1 = vx + dt * ax, vz + dt * az, om + dt * al
+    return [px + dt * vx1, pz + dt * vz1, th + dt * om1, vx1, vz1, om1]
+
+
+def quadrotor_step_jacobian(x, u, p):
+    """6x8 Jacobian of quadrotor_step w.r.t. [x; u], derived by hand; structural
+    zeros are the float 0.0."""
+    th = x[2]
+    dt, m, arm, I = p["dt"], p["mass"], p["arm"], p["inertia"]
+    s, c = T.sin(th), T.cos(th)
+    thrust = u[0] + u[1]
+    J = [[0.0] * 8 for _ in range(6)]
+    # velocities
+    dvx_dth = -dt * thrust * c / m
+    dvz_dth = -dt * thrust * s / m
+    dvx_du = -dt * s / m
+    dvz_du = dt * c / m
+    dom_du = (dt * arm / I, -dt * arm / I)
+    J[3][3] = 1.0
+    J[3][2] = dvx_dth
+    J[4][4] = 1.0
+    J[4][2] = dvz_dth
+    J[5][5] = 1.0
+    for j in range(2):
+        J[3][6 + j] = dvx_du
+        J[4][6 + j] = dvz_du
+        J[5][6 + j] = dom_du[j]
+    # positions and angle: p+ = p + dt * v+
+    J[0][0] = 1.0
+    J[0][2] = dt * dvx_dth
+    J[0][3] = dt
+    J[1][1] = 1.0
+    J[1][2] = dt * dvz_dth
+    J[1][4] = dt
+    J[2][2] = 1.0
+    J[2][5] = dt
+    for j in range(2):
+        J[0][6 + j] = dt * dvx_du
+        J[1][6 + j] = dt * dvz_du
+        J[2][6 + j] = dt * dom_du[j]
+    return J
+
+
+def kkt_order(Tn: int):
+    """Stage ordering of the KKT unknowns: x0, lam0, then per stage k:
+    u_k, x_{k+1}, lam_{k+1}.  Entries are (kind, stage, component).
+
+    Every state block is eliminated before the multipliers of the constraint
+    that defines it, so each multiplier pivot block picks up -(2Q)^-1 and stays
+    well away from zero (placing lam_{k+1} before x_{k+1} instead leaves pivots
+    of size delta, i.e. element growth of 1/delta)."""
+    order = [("x", 0, i) for i in range(6)] + [("l", 0, i) for i in range(6)]
+    for k in range(Tn):
+        order += [("u", k, j) for j in range(2)]
+        order += [("x", k + 1, i) for i in range(6)]
+        order += [("l", k + 1, i) for i in range(6)]
+    return order
+
+
+def ldlt_solve(K, rhs, g, tag_pivots: bool):
+    """Solve K s = rhs by an unrolled LDL^T factorisation without pivoting.
+
+    K is a dense list-of-lists whose structural zeros are the float 0.0; the
+    tracer drops every product with a structural zero, so only the fill that
+    the ordering creates is ever computed.  Pivots, and every division by a
+    pivot, are tagged FP64 when tag_pivots (mixed precision)."""
+    from contextlib import nullcontext
+    n = len(K)
+    f64 = g.fp64 if tag_pivots else nullcontext
+    L = [dict() for _ in range(n)]       # L[i][k], k < i, non-zeros only
+    d = [None] * n
+    cols = [set() for _ in range(n)]     # rows i > j with L[i][j] != 0
+    for j in range(n):
+        v = {k: L[j][k] * d[k] for k in L[j]}
+        with f64():
+            dj = K[j][j]
+            for k in sorted(L[j]):
+                dj = dj - L[j][k] * v[k]
+            d[j] = dj
+        # candidate rows: structural non-zeros of column j, plus fill from shared k
+        rows = {i for i in range(j + 1, n) if not (isinstance(K[i][j], float) and K[i][j] == 0.0)}
+        for k in L[j]:
+            rows |= {i for i in cols[k] if i > j}
+        for i in sorted(rows):
+            s = K[i][j]
+            for k in sorted(L[i].keys() & L[j].keys()):
+                s = s - L[i][k] * v[k]
+            if isinstance(s, float) and s == 0.0:
+                continue
+            with f64():
+                L[i][j] = s / d[j]
+            cols[j].add(i)
+    y = [None] * n
+    for i in range(n):
+        acc = rhs[i]
+        for k in sorted(L[i]):
+            acc = acc - L[i][k] * y[k]
+        y[i] = acc
+    with f64():
+        w = [y[i] / d[i] for i in range(n)]
+    s = [None] * n
+    for i in reversed(range(n)):
+        acc = w[i]
+        for r in sorted(cols[i]):
+            acc = acc - L[r][i] * s[r]
+        s[i] = acc
+    return s
+
+
+def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool = False) -> ProgramIR:
+    """Closed-form MPC (Eq. 8: M fixed solver iterations, no branches).
+
+    Problem: states x_0..x_T, thrusts u_0..u_{T-1} of the planar quadrotor,
+    x_0 = x0bar, x_{k+1} = step(x_k, u_k); cost sum_k (x_k - x_ref)' Q (x_k - x_ref)
+    + sum_k (u_k - u_h)' R (u_k - u_h), u_h = m g / 2, x_ref = (wx, wz, 0, 0, 0, 0);
+    thrust bounds 0 < u < u_max by the log barrier -mu sum [log u + log(u_max - u)].
+    Iteration i (mu_i = mu0 (mu_end / mu0)^(i / (M-1))): Gauss-Newton Hessian
+    (cost + barrier, dynamics curvature dropped), linearised constraints, KKT
+    system [[H, A'], [A, -delta I]] solved by ldlt_solve in the stage ordering,
+    step length alpha = min(1, tau * fraction-to-boundary), z += alpha dz.
+    Initial guess: u = u_h and the rollout of u_h from x0bar.
+    Inputs: x0bar (6), waypoint (2).  Output: z = (x_0..x_T, u_0..u_{T-1}).
+    debug_first_step: output the first KKT solution (in kkt_order) instead.
+    """
+    from contextlib import nullcontext
+    p = dict(QUADROTOR)
+    if params:
+        p.update(params)
+    Tn, M = p["T"], p["M"]
+    g = T.Graph()
+    x0bar = g.symbols(6)
+    wp = g.symbols(2)
+    uh = p["mass"] * p["g"] / 2.0
+    umax = p["u_max"]
+    f64 = g.fp64 if mixed_tags else nullcontext
+    xref = [wp[0], wp[1], 0.0, 0.0, 0.0, 0.0]
+    u = [[uh, uh] for _ in range(Tn)]
+    x = [list(x0bar)]
+    for k in range(Tn):
+        x.append(quadrotor_step(x[k], u[k], p))
+    order = kkt_order(Tn)
+    pos = {e: i for i, e in enumerate(order)}
+    n = len(order)
+    first = None
+    for it in range(M):
+        mu = p["mu0"] * (p["mu_end"] / p["mu0"]) ** (it / (M - 1)) if M > 1 else p["mu0"]
+        K = [[0.0] * n for _ in range(n)]
+        rhs = [0.0] * n
+        for k in range(Tn + 1):
+            for i in range(6):
+                a = pos[("x", k, i)]
+                K[a][a] = 2.0 * p["q"][i]
+                rhs[a] = -2.0 * p["q"][i] * (x[k][i] - xref[i])
+        for k in range(Tn):
+            for j in range(2):
+                a = pos[("u", k, j)]
+                uk = u[k][j]
+                with f64():
+                    inv_lo = 1.0 / uk
+                    inv_hi = 1.0 / (umax - uk)
+                    hb = mu * (inv_lo * inv_lo + inv_hi * inv_hi)
+                    gb = mu * (inv_lo - inv_hi)
+                K[a][a] = 2.0 * p["r"] + hb
+                rhs[a] = -(2.0 * p["r"] * (uk - uh) - gb)
+        # constraints: lam0 -> x0 - x0bar;  lam_{k+1} -> x_{k+1} - step(x_k, u_k)
+        for i in range(6):
+            li, xi = pos[("l", 0, i)], pos[("x", 0, i)]
+            K[li][xi] = K[xi][li] = 1.0
+            K[li][li] = -p["delta"]
+            rhs[li] = -(x[0][i] - x0bar[i])
+        for k in range(Tn):
+            fk = quadrotor_step(x[k], u[k], p)
+            J = quadrotor_step_jacobian(x[k], u[k], p)
+            for i in range(6):
+                li = pos[("l", k + 1, i)]
+                K[li][li] = -p["delta"]
+                xn = pos[("x", k + 1, i)]
+                K[li][xn] = K[xn][li] = 1.0
+                for j in range(8):
+                    col = pos[("x", k, j)] if j < 6 else pos[("u", k, j - 6)]
+                    dv = J[i][j]
+                    if isinstance(dv, float) and dv == 0.0:
+                        continue
+                    K[li][col] = K[col][li] = -dv
+                rhs[li] = -(x[k + 1][i] - fk[i])
+        s = ldlt_solve(K, rhs, g, mixed_tags)
+        if it == 0:
+            first = s
+            if debug_first_step:
+                break
+        dx = [[s[pos[("x", k, i)]] for i in range(6)] for k in range(Tn + 1)]
+        du = [[s[pos[("u", k, j)]] for j in range(2)] for k in range(Tn)]
+        # fraction to the boundary of 0 < u < u_max, branch-free
+        ratio = None
+        for k in range(Tn):
+            for j in range(2):
+                lo = u[k][j] / T.fmax(-du[k][j], 0.0)
+                hi = (umax - u[k][j]) / T.fmax(du[k][j], 0.0)
+                r = T.fmin(lo, hi)
+                ratio = r if ratio is None else T.fmin(ratio, r)
+        alpha = T.fmin(1.0, p["tau"] * ratio)
+        x = [[x[k][i] + alpha * dx[k][i] for i in range(6)] for k in range(Tn + 1)]
+        u = [[u[k][j] + alpha * du[k][j] for j in range(2)] for k in range(Tn)]
+    ins = [("x0", x0bar), ("waypoint", wp)]
+    if debug_first_step:
+        return T.Function(ins, [("kkt_solution", first)]).to_ir()
+    z = [v for k in range(Tn + 1) for v in x[k]] + [v for k in range(Tn) for v in u[k]]
+    return T.Function(ins, [("z", z)]).to_ir()

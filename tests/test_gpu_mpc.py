@@ -1,0 +1,85 @@
+"""GPU parity of the closed-form MPC program (unrolled barrier-Newton with an
+unrolled LDL^T per iteration) in FP64, FP32 and mixed precision.
+
+Tolerances: FP64 kernels vs the FP64 oracle: max(1e-12 * s_k, 2 * B_k,i);
+FP32 and mixed kernels vs the FP64 oracle: max(2e-4 * s_k, 2 * B32_k,i) (the
+FP32 bound covers mixed, whose FP64-tagged ops are only more accurate).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import MODE_MIXED, Oracle, tolerance
+from paper_2408_09662_gb300 import programs
+from paper_2408_09662_gb300.api import Function
+
+pytestmark = pytest.mark.gpu
+
+
+def mpc_inputs(N, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.vstack([rng.uniform(-0.5, 0.5, (6, N)), rng.uniform(-1, 1, (2, N))])
+
+
+@pytest.fixture(scope="module")
+def mpc():
+    return programs.quadrotor_mpc().to_bytes()
+
+
+def _run(fn, X):
+    x = torch.tensor(X, dtype=fn.torch_dtype, device="cuda")
+    y = fn(x)
+    torch.cuda.synchronize()
+    return y.double().cpu().numpy()
+
+
+def _check(y, ref, tol):
+    bad = ~(np.abs(y - ref) <= tol)
+    assert not np.any(bad), (int(bad.sum()), float(np.max(np.abs(y - ref) - tol)))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "mixed", "f32"])
+def test_mpc_full_batch_sampled(mpc, dtype):
+    """N = 16384 instances; the program is split over two kernels that pass
+    their live values through the workspace."""
+    N = 16384
+    X = mpc_inputs(N, seed=1)
+    fn = Function(mpc, dtype=dtype)
+    assert fn.info.n_segments >= 2
+    if dtype != "f64":
+        X = X.astype(np.float32).astype(np.float64)
+    y = _run(fn, X)
+    assert np.all(np.isfinite(y))
+    assert np.all((y[66:] > 0) & (y[66:] < 15))
+    idx = np.unique(np.concatenate([np.random.default_rng(2).choice(N, 96, replace=False),
+                                    [0, N - 1]]))
+    orc = Oracle(mpc)
+    ref = orc.eval(X[:, idx])
+    if dtype == "f64":
+        tol = tolerance(orc, X[:, idx], ref, 1e-12, kind=0)
+    else:
+        tol = tolerance(orc, X[:, idx], ref, 2e-4, kind=1)
+    _check(y[:, idx], ref, tol)
+
+
+def test_mixed_tracks_its_emulation_more_closely_than_fp32(mpc):
+    N = 2048
+    X = mpc_inputs(N, seed=3).astype(np.float32).astype(np.float64)
+    orc = Oracle(mpc)
+    ref64 = orc.eval(X)
+    refm = orc.eval(X, mode=MODE_MIXED)
+    ym = _run(Function(mpc, dtype="mixed"), X)
+    scale = np.max(np.abs(ref64), axis=1, keepdims=True)
+    # the GPU's mixed result and the oracle's mixed emulation round the same
+    # FP32 ops, so they agree far better than either agrees with FP64
+    assert np.max(np.abs(ym - refm) / scale) < 2e-5
+    assert np.max(np.abs(ym - ref64) / scale) < 2e-4
+
+
+def test_mpc_interpreter_matches(mpc):
+    N = 1000
+    X = mpc_inputs(N, seed=4)
+    y = _run(Function(mpc, dtype="f64", path="interp"), X)
+    orc = Oracle(mpc)
+    ref = orc.eval(X)
+    _check(y, ref, tolerance(orc, X, ref, 1e-12, kind=0))

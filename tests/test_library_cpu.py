@@ -201,7 +201,7 @@ def test_adjoint_source_generates_reduction_for_broadcast_inputs():
     try:
         src = L.cusadi_source(fn, adjoint=True)
         assert "__shfl_xor_sync" in src and "atomicAdd(&Yb[2ll * ldy]" in src
-        assert "atomicAdd(&Yb[3ll * ldy]" in src and "cs_adj_zero" in src
+        assert "atomicAdd(&Yb[3ll * ldy]" in src and "cs_adj_f64_zero" in src
         assert L.cusadi_info(fn).n_bcast_in == 2
         counts = L.cusadi_op_counts(fn, adjoint=True)
         assert counts[Op.COS] == 1
