@@ -109,6 +109,8 @@ typedef struct {
 #define CUSADI_ADJ_ACCUMULATE 1u        /* add into in_bar instead of overwriting it */
 #define CUSADI_ADJ_REDUCE_BROADCAST 2u  /* sum broadcast inputs' adjoints over instances
                                            into column 0 of their rows */
+#define CUSADI_ADJ_ACCUMULATE_BROADCAST 4u  /* with REDUCE_BROADCAST: add the sums into column 0
+                                               (other rows are still overwritten) */
 
 /* Fills *opt with the defaults quoted above. */
 void cusadi_default_options(cusadi_options* opt);
@@ -155,7 +157,9 @@ cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out
  * CUSADI_ADJ_REDUCE_BROADCAST, broadcast input rows receive the sum over
  * instances in column 0 (accumulated with atomics, so the summation order and
  * the last bits vary run to run); otherwise they receive per-instance values.
- * Without CUSADI_ADJ_ACCUMULATE the written entries are overwritten.
+ * Without CUSADI_ADJ_ACCUMULATE the written entries are overwritten, except the
+ * reduced rows under CUSADI_ADJ_ACCUMULATE_BROADCAST (gradient accumulation of
+ * a shared parameter over many calls, e.g. the steps of a rollout).
  * workspace: cusadi_workspace_bytes(fn, N, 1) bytes. */
 cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,
                              int64_t ld_ob, void* in_bar, int64_t ld_ib, int64_t N,

@@ -201,3 +201,64 @@ def quadrotor_mpc(x0bar, wp, M=None, **over):
         x = [x[k] + alpha * dx[k] for k in range(Tn + 1)]
         u = [u[k] + alpha * du[k] for k in range(Tn)]
     return np.concatenate([np.concatenate(x), np.concatenate(u)])
+
+
+# ---------------------------------------------------------------------------
+# single-rigid-body quadruped under u = u_grav - K x, RK4, running loss
+# (vectorised over instances: arrays [12, N])
+# ---------------------------------------------------------------------------
+SRB = dict(mass=12.0, inertia=(0.07, 0.26, 0.28), g=9.81, dt=0.005,
+           feet=((0.2, 0.15, -0.3), (0.2, -0.15, -0.3), (-0.2, 0.15, -0.3), (-0.2, -0.15, -0.3)))
+
+
+def _rz_ry_rx(phi, th, psi):
+    """[3, 3, N] rotation Rz(psi) @ Ry(th) @ Rx(phi), built from the factors."""
+    N = np.shape(phi)[0]
+    one, zero = np.ones(N), np.zeros(N)
+    Rx = np.array([[one, zero, zero], [zero, np.cos(phi), -np.sin(phi)], [zero, np.sin(phi), np.cos(phi)]])
+    Ry = np.array([[np.cos(th), zero, np.sin(th)], [zero, one, zero], [-np.sin(th), zero, np.cos(th)]])
+    Rz = np.array([[np.cos(psi), -np.sin(psi), zero], [np.sin(psi), np.cos(psi), zero], [zero, zero, one]])
+    return np.einsum("abn,bcn,cdn->adn", Rz, Ry, Rx)
+
+
+def srb_f(x, u, p=SRB):
+    pos, ang, v, w = x[0:3], x[3:6], x[6:9], x[9:12]
+    R = _rz_ry_rx(ang[0], ang[1], ang[2])
+    Ib = np.array(p["inertia"])
+    Iw = np.einsum("akn,k,bkn->abn", R, Ib, R)
+    F = np.zeros_like(v)
+    tau = np.zeros_like(v)
+    for i, foot in enumerate(p["feet"]):
+        r = np.einsum("akn,k->an", R, np.array(foot))
+        f = u[3 * i:3 * i + 3]
+        F = F + f
+        tau = tau + np.cross(r, f, axis=0)
+    Iww = np.einsum("abn,bn->an", Iw, w)
+    rhs = tau - np.cross(w, Iww, axis=0)
+    wd = np.stack([np.linalg.solve(Iw[:, :, n], rhs[:, n]) for n in range(x.shape[1])], axis=1)
+    vd = F / p["mass"] - np.array([0, 0, p["g"]])[:, None]
+    phi, th, psi = ang
+    # world angular velocity = E(Theta) dTheta/dt for ZYX angles; invert E
+    E = np.array([[np.cos(psi) * np.cos(th), -np.sin(psi), np.zeros_like(psi)],
+                  [np.sin(psi) * np.cos(th), np.cos(psi), np.zeros_like(psi)],
+                  [-np.sin(th), np.zeros_like(psi), np.ones_like(psi)]])
+    angd = np.stack([np.linalg.solve(E[:, :, n], w[:, n]) for n in range(x.shape[1])], axis=1)
+    return np.vstack([v, angd, vd, wd])
+
+
+def srb_rollout_loss(x0, K, steps=50, p=SRB):
+    """sum over instances and t = 1..steps of ||x_t||^2, u = u_grav - K x held per RK4 step."""
+    x = np.array(x0, dtype=np.float64)
+    ug = np.zeros((12, 1))
+    ug[2::3] = p["mass"] * p["g"] / 4
+    total = 0.0
+    dt = p["dt"]
+    for _ in range(steps):
+        u = ug - K @ x
+        k1 = srb_f(x, u, p)
+        k2 = srb_f(x + 0.5 * dt * k1, u, p)
+        k3 = srb_f(x + 0.5 * dt * k2, u, p)
+        k4 = srb_f(x + dt * k3, u, p)
+        x = x + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        total += float(np.sum(x * x))
+    return total, x

@@ -28,6 +28,7 @@ CUSADI_F64, CUSADI_F32, CUSADI_MIXED = 0, 1, 2
 CUSADI_PATH_AUTO, CUSADI_PATH_COMPILED, CUSADI_PATH_INTERP = 0, 1, 2
 CUSADI_ADJ_ACCUMULATE = 1
 CUSADI_ADJ_REDUCE_BROADCAST = 2
+CUSADI_ADJ_ACCUMULATE_BROADCAST = 4
 
 
 class cusadi_options(ctypes.Structure):

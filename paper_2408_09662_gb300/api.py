@@ -119,8 +119,10 @@ class Function:
         return out
 
     def adjoint(self, x: torch.Tensor, ybar: torch.Tensor, out: torch.Tensor | None = None,
-                accumulate: bool = False, reduce_broadcast: bool = False) -> torch.Tensor:
-        """x_bar = J(x)^T y_bar per instance (broadcast rows summed when reduce_broadcast)."""
+                accumulate: bool = False, reduce_broadcast: bool = False,
+                accumulate_broadcast: bool = False) -> torch.Tensor:
+        """x_bar = J(x)^T y_bar per instance (broadcast rows summed when reduce_broadcast;
+        accumulate_broadcast adds those sums into out instead of overwriting them)."""
         self._check(x, self.nnz_in, "x")
         N = x.shape[1]
         self._check(ybar, self.nnz_out, "ybar")
@@ -129,7 +131,8 @@ class Function:
                 (self.nnz_in, N), dtype=self.torch_dtype, device=x.device)
         self._check(out, self.nnz_in, "out")
         flags = (L.CUSADI_ADJ_ACCUMULATE if accumulate else 0) | \
-                (L.CUSADI_ADJ_REDUCE_BROADCAST if reduce_broadcast else 0)
+                (L.CUSADI_ADJ_REDUCE_BROADCAST if reduce_broadcast else 0) | \
+                (L.CUSADI_ADJ_ACCUMULATE_BROADCAST if accumulate_broadcast else 0)
         ws = self.workspace(N, True, x.device)
         L.cusadi_adjoint(self._fn, x.data_ptr(), self._ld(x), ybar.data_ptr(), self._ld(ybar),
                          out.data_ptr(), self._ld(out), N, flags,

@@ -553,7 +553,7 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
                              uint32_t flags, void* workspace, cusadi_stream stream) {
   if (!fn) return fail(CUSADI_E_INVALID_ARG, "fn is NULL");
   if (N < 0) return fail(CUSADI_E_INVALID_ARG, "N must be >= 0");
-  if (flags & ~(CUSADI_ADJ_ACCUMULATE | CUSADI_ADJ_REDUCE_BROADCAST))
+  if (flags & ~(CUSADI_ADJ_ACCUMULATE | CUSADI_ADJ_REDUCE_BROADCAST | CUSADI_ADJ_ACCUMULATE_BROADCAST))
     return fail(CUSADI_E_INVALID_ARG, "unknown adjoint flags");
   cusadi_status s = ensure_adjoint(fn);
   if (s != CUSADI_OK) return s;
@@ -571,7 +571,8 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
   if (s != CUSADI_OK) return s;
   const int acc = (flags & CUSADI_ADJ_ACCUMULATE) ? 1 : 0;
   const bool has_reduce = fn->path == CUSADI_PATH_INTERP ? fn->adj.ip.has_reduce : fn->adj.cg.has_reduce;
-  if (reduce && !acc && has_reduce) {
+  const bool acc_bcast = acc || (flags & CUSADI_ADJ_ACCUMULATE_BROADCAST);
+  if (reduce && !acc_bcast && has_reduce) {
     if (fn->path == CUSADI_PATH_INTERP) {
       // clear column 0 of the broadcast rows
       const size_t e = elt_io(fn->opt.dtype);

@@ -402,3 +402,72 @@ def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool =
         return T.Function(ins, [("kkt_solution", first)]).to_ir()
     z = [v for k in range(Tn + 1) for v in x[k]] + [v for k in range(Tn) for v in u[k]]
     return T.Function(ins, [("z", z)]).to_ir()
+
+
+# ---------------------------------------------------------------------------
+# Differentiable rollout: single-rigid-body quadruped under linear feedback
+# ---------------------------------------------------------------------------
+SRB = dict(mass=12.0, inertia=(0.07, 0.26, 0.28), g=9.81, dt=0.005,
+           feet=((0.2, 0.15, -0.3), (0.2, -0.15, -0.3), (-0.2, 0.15, -0.3), (-0.2, -0.15, -0.3)))
+
+
+def _rot_zyx(phi, th, psi):
+    """R = Rz(psi) Ry(th) Rx(phi) (body -> world)."""
+    cf, sf = T.cos(phi), T.sin(phi)
+    ct, st = T.cos(th), T.sin(th)
+    cp, sp = T.cos(psi), T.sin(psi)
+    return [[cp * ct, cp * st * sf - sp * cf, cp * st * cf + sp * sf],
+            [sp * ct, sp * st * sf + cp * cf, sp * st * cf - cp * sf],
+            [-st, ct * sf, ct * cf]]
+
+
+def srb_dynamics(x, u, p):
+    """State [p(3), Theta(3) = roll, pitch, yaw (ZYX), v(3), omega(3)], world-frame
+    velocities; u = four world-frame foot forces at body-fixed feet."""
+    pos, ang, v, w = x[0:3], x[3:6], x[6:9], x[9:12]
+    R = _rot_zyx(*ang)
+    Ib = p["inertia"]
+    # I_w^-1 = R Ib^-1 R'
+    Iinv = [[sum(R[a][k] * R[b][k] / Ib[k] for k in range(3)) for b in range(3)] for a in range(3)]
+    Iw = [[sum(R[a][k] * R[b][k] * Ib[k] for k in range(3)) for b in range(3)] for a in range(3)]
+    F = [0.0, 0.0, 0.0]
+    tau = [0.0, 0.0, 0.0]
+    for i, foot in enumerate(p["feet"]):
+        r = [sum(R[a][k] * foot[k] for k in range(3)) for a in range(3)]
+        f = u[3 * i:3 * i + 3]
+        F = [F[a] + f[a] for a in range(3)]
+        tau = [tau[0] + r[1] * f[2] - r[2] * f[1], tau[1] + r[2] * f[0] - r[0] * f[2],
+               tau[2] + r[0] * f[1] - r[1] * f[0]]
+    Iww = [sum(Iw[a][b] * w[b] for b in range(3)) for a in range(3)]
+    gyro = [w[1] * Iww[2] - w[2] * Iww[1], w[2] * Iww[0] - w[0] * Iww[2], w[0] * Iww[1] - w[1] * Iww[0]]
+    rhs = [tau[a] - gyro[a] for a in range(3)]
+    wd = [sum(Iinv[a][b] * rhs[b] for b in range(3)) for a in range(3)]
+    vd = [F[0] / p["mass"], F[1] / p["mass"], F[2] / p["mass"] - p["g"]]
+    phi, th, psi = ang
+    cp, sp, ct, st = T.cos(psi), T.sin(psi), T.cos(th), T.sin(th)
+    a = (cp * w[0] + sp * w[1]) / ct
+    angd = [a, -sp * w[0] + cp * w[1], w[2] + st * a]
+    return list(v) + angd + vd + wd
+
+
+def srb_step(params=None) -> ProgramIR:
+    """One RK4 step (dt, force held) of the SRB under u = u_grav - K x, plus the
+    running loss.  Inputs: K (144, broadcast: one gain shared by all instances,
+    row-major 12x12), x (12), L (1).  Outputs: x+ (12), L + ||x+||^2 (1).
+    Output rows line up with input rows 144..156, so a rollout can ping-pong
+    two buffers without copies."""
+    from .ir import ARG_BROADCAST
+    p = dict(SRB)
+    if params:
+        p.update(params)
+    g = T.Graph()
+    K = g.symbols(144)
+    x = g.symbols(12)
+    (L,) = g.symbols(1)
+    ug = p["mass"] * p["g"] / 4.0
+    u = [(ug if j % 3 == 2 else 0.0) - sum(K[12 * j + k] * x[k] for k in range(12))
+         for j in range(12)]
+    xn = rk4_step(lambda s, uu: srb_dynamics(s, uu, p), x, u, p["dt"])
+    Ln = L + sum(v * v for v in xn)
+    return T.Function([("K", K, ARG_BROADCAST), ("x", x), ("L", [L])],
+                      [("x_next", xn), ("L_next", [Ln])]).to_ir()

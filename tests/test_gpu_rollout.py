@@ -1,0 +1,99 @@
+"""Differentiable SRB-quadruped rollout on the GPU: 50 RK4 steps of a linear
+feedback policy with a shared 12x12 gain, loss = sum of squared states.
+
+Checks: the loss and final state against the numpy model; dL/dK and dL/dx0
+against central differences of the numpy model (h = 1e-6, FP64) and against
+the oracle's reverse sweep of each step; checkpointed == stored-state
+gradients (x_bar bitwise; K_bar up to atomic summation order).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import Oracle
+from oracle import models as M
+from paper_2408_09662_gb300 import programs
+from paper_2408_09662_gb300.api import Function
+from paper_2408_09662_gb300.rollout import StepProgram, rollout
+
+pytestmark = pytest.mark.gpu
+STEPS = 50
+
+
+def srb_inputs(N, seed=0):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-0.1, 0.1, (12, N)), rng.normal(0.0, 0.1, (12, 12))
+
+
+@pytest.fixture(scope="module")
+def prog64():
+    return StepProgram(Function(programs.srb_step(), dtype="f64"), 144, 12)
+
+
+def _grad(prog, x0, K, ce):
+    x = torch.tensor(x0, dtype=prog.fn.torch_dtype, device="cuda", requires_grad=True)
+    k = torch.tensor(K.reshape(144), dtype=prog.fn.torch_dtype, device="cuda", requires_grad=True)
+    L, xT = rollout(prog, x, k, STEPS, checkpoint_every=ce)
+    L.backward()
+    return float(L), xT.detach().cpu().numpy(), x.grad.cpu().numpy(), k.grad.cpu().numpy().reshape(12, 12)
+
+
+def test_rollout_loss_matches_numpy_model(prog64):
+    x0, K = srb_inputs(64, seed=1)
+    L, xT, _, _ = _grad(prog64, x0, K, 10)
+    ref_L, ref_x = M.srb_rollout_loss(x0, K, STEPS)
+    assert abs(L - ref_L) <= 1e-11 * abs(ref_L)
+    np.testing.assert_allclose(xT, ref_x, rtol=1e-10, atol=1e-12)
+
+
+def test_rollout_gradient_matches_central_differences(prog64):
+    N = 16
+    x0, K = srb_inputs(N, seed=2)
+    _, _, gx, gK = _grad(prog64, x0, K, 10)
+    h = 1e-6
+    rng = np.random.default_rng(3)
+    for (a, b) in [tuple(rng.integers(12, size=2)) for _ in range(16)]:
+        Kp, Km = K.copy(), K.copy()
+        Kp[a, b] += h
+        Km[a, b] -= h
+        fd = (M.srb_rollout_loss(x0, Kp, STEPS)[0] - M.srb_rollout_loss(x0, Km, STEPS)[0]) / (2 * h)
+        assert abs(gK[a, b] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(gK))), (a, b, gK[a, b], fd)
+    for k in range(12):
+        xp, xm = x0.copy(), x0.copy()
+        xp[k, 5] += h
+        xm[k, 5] -= h
+        fd = (M.srb_rollout_loss(xp, K, STEPS)[0] - M.srb_rollout_loss(xm, K, STEPS)[0]) / (2 * h)
+        assert abs(gx[k, 5] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(gx))), (k, gx[k, 5], fd)
+
+
+def test_step_adjoint_matches_oracle_reverse_sweep(prog64):
+    N = 2048
+    x0, K = srb_inputs(N, seed=4)
+    X = np.vstack([np.tile(K.reshape(144, 1), (1, N)), x0, np.zeros((1, N))])
+    ybar = np.random.default_rng(5).standard_normal((13, N))
+    ref = Oracle(programs.srb_step().to_bytes()).adjoint(X, ybar)
+    fn = prog64.fn
+    xb = fn.adjoint(torch.tensor(X, device="cuda"), torch.tensor(ybar, device="cuda"),
+                    reduce_broadcast=True).cpu().numpy()
+    s = np.max(np.abs(ref[144:]))
+    np.testing.assert_allclose(xb[144:], ref[144:], rtol=0, atol=1e-12 * s)
+    Kref = ref[:144].sum(axis=1)
+    np.testing.assert_allclose(xb[:144, 0], Kref, rtol=1e-11, atol=1e-12 * np.max(np.abs(Kref)))
+
+
+def test_checkpointing_does_not_change_the_gradient(prog64):
+    x0, K = srb_inputs(512, seed=6)
+    L1, _, gx1, gK1 = _grad(prog64, x0, K, 10)
+    L2, _, gx2, gK2 = _grad(prog64, x0, K, 1)      # every state stored, no recompute
+    assert L1 == L2
+    np.testing.assert_array_equal(gx1, gx2)
+    np.testing.assert_allclose(gK1, gK2, rtol=1e-12)
+
+
+def test_fp32_rollout_gradient_close_to_fp64(prog64):
+    x0, K = srb_inputs(1024, seed=7)
+    prog32 = StepProgram(Function(programs.srb_step(), dtype="f32"), 144, 12)
+    L64, _, gx64, gK64 = _grad(prog64, x0, K, 10)
+    L32, _, gx32, gK32 = _grad(prog32, x0, K, 10)
+    assert abs(L32 - L64) <= 1e-4 * abs(L64)
+    assert np.max(np.abs(gK32 - gK64)) <= 2e-3 * np.max(np.abs(gK64))
