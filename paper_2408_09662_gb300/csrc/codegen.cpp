@@ -281,6 +281,28 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
       }
     }
     std::string name = o.prefix + "_" + std::to_string(s);
+    if (o.device_fn) {
+      // one instance per call; the caller owns the index and the bounds check
+      src << "extern \"C\" __device__ void " << name << "(\n"
+          << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
+          << "* __restrict__ X2, long long ldx2, " << tin
+          << "* __restrict__ Y, long long ldy,\n    " << tw
+          << "* __restrict__ W, long long ldw, long long i) {\n"
+          << "  const bool active = true;\n  const int acc = 0, reduce = 0;\n"
+          << "  const " << tin << "* __restrict__ Xb = X;\n"
+          << "  const " << tin << "* __restrict__ X2b = X2;\n"
+          << "  " << tin << "* __restrict__ Yb = Y;\n"
+          << "  X += i; X2 += i; Y += i; W += i;\n"
+          << "  (void)Xb; (void)X2b; (void)Yb; (void)W; (void)ldw; (void)ldx2; (void)acc; (void)reduce; (void)active;\n"
+          << body.str() << "}\n";
+      Segment S;
+      S.begin = segs[s].first;
+      S.end = segs[s].second;
+      S.name = name;
+      S.source = src.str();
+      R.segs.push_back(std::move(S));
+      continue;
+    }
     src << "extern \"C\" __global__ void __launch_bounds__(" << o.block << ") " << name << "(\n"
         << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
         << "* __restrict__ X2, long long ldx2, " << tin

@@ -100,6 +100,7 @@ struct CodegenOptions {
   bool inline_math = false;
   bool adjoint = false;
   int64_t split = -1;            // input rows >= split come from the second buffer
+  bool device_fn = false;        // emit relocatable __device__ functions of one instance
   std::string prefix = "cs_fwd";
 };
 
