@@ -165,6 +165,31 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
                              int64_t ld_ob, void* in_bar, int64_t ld_ib, int64_t N,
                              uint32_t flags, void* workspace, cusadi_stream stream);
 
+/* Size of the static scratch region behind cusadi_eval_noalloc, in bytes. */
+#define CUSADI_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* cusadi_eval for callers that must not allocate device memory: code that
+ * runs under a no-allocation rule after start-up (a real-time control loop
+ * calling the MPC every tick) or inside a CUDA stream capture, where
+ * cudaMalloc is not allowed.  The paper has no counterpart.
+ *
+ * Same arguments and results as cusadi_eval minus the workspace: the
+ * workspace is a file-scope device array of CUSADI_NOALLOC_SCRATCH_BYTES that
+ * every GPU which loads this library keeps until the process exits.  The call
+ * allocates nothing: it calls no cudaMalloc/cudaFree and no allocating library
+ * routine.  Set-up: the first call on a device looks up the array's device
+ * address there (cudaGetSymbolAddress, once per device), so make that first
+ * call before any stream capture; the function's kernels must already be
+ * loaded on the device, which any earlier cusadi_eval of it does (otherwise
+ * INVALID_ARG).  Evaluations whose workspace exceeds the scratch size
+ * (cusadi_workspace_bytes(fn, N, 0) > CUSADI_NOALLOC_SCRATCH_BYTES) are
+ * rejected with INVALID_ARG; evaluate fewer instances per call.  Every call
+ * shares the one array and it keeps the last call's contents; nothing in it
+ * needs to start at zero (each value is written before it is read), but calls
+ * that overlap on the GPU (different streams, or several threads) race on it. */
+cusadi_status cusadi_eval_noalloc(cusadi_fn fn, const void* in, int64_t ld_in, void* out,
+                                  int64_t ld_out, int64_t N, cusadi_stream stream);
+
 /* Writes the generated CUDA source of kernel `segment` (adjoint = 1: of the
  * adjoint kernels) into buf (NUL-terminated, truncated to *len bytes); sets *len
  * to the full size + 1.  UNSUPPORTED on the interpreter path. */

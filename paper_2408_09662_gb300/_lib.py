@@ -29,6 +29,7 @@ CUSADI_PATH_AUTO, CUSADI_PATH_COMPILED, CUSADI_PATH_INTERP = 0, 1, 2
 CUSADI_ADJ_ACCUMULATE = 1
 CUSADI_ADJ_REDUCE_BROADCAST = 2
 CUSADI_ADJ_ACCUMULATE_BROADCAST = 4
+CUSADI_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class cusadi_options(ctypes.Structure):
@@ -72,6 +73,7 @@ SIGNATURES = {
     "cusadi_eval": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
     "cusadi_adjoint": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                  c_int64, c_uint32, c_void_p, c_void_p]),
+    "cusadi_eval_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p]),
     "cusadi_source": (c_int32, [c_void_p, ctypes.c_int, ctypes.c_int, c_char_p, ctypes.POINTER(c_size_t)]),
     "cusadi_status_string": (c_char_p, [c_int32]),
     "cusadi_last_error": (c_char_p, []),
@@ -152,6 +154,11 @@ def cusadi_adjoint(fn: int, inp: int, ld_in: int, out_bar: int, ld_ob: int, in_b
                    ld_ib: int, N: int, flags: int, workspace: int, stream: int) -> None:
     check(lib().cusadi_adjoint(fn, inp, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, flags,
                                workspace, stream), "cusadi_adjoint")
+
+
+def cusadi_eval_noalloc(fn: int, inp: int, ld_in: int, out: int, ld_out: int, N: int,
+                        stream: int) -> None:
+    check(lib().cusadi_eval_noalloc(fn, inp, ld_in, out, ld_out, N, stream), "cusadi_eval_noalloc")
 
 
 def cusadi_source(fn: int, adjoint: bool = False, segment: int = 0) -> str:

@@ -23,7 +23,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 HOST_SRC = ["ir.cpp", "passes.cpp", "codegen.cpp", "interp.cpp", "runtime.cpp"]
-DEVICE_SRC = ["kernels.cu"]
+DEVICE_SRC = ["kernels.cu", "noalloc.cu"]
 
 
 def _sources():

@@ -133,4 +133,11 @@ int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, con
 // threads per block of the shared-memory interpreter (0: work vector too long)
 int interp_block(int64_t n_slots, int dtype);
 
+// runtime.cpp: records msg as this thread's last error and returns s
+cusadi_status report(cusadi_status s, const std::string& msg);
+// runtime.cpp: forward evaluation using `scratch` as the workspace, loading nothing
+cusadi_status eval_in_scratch(cusadi_fn fn, const void* in, int64_t ld_in, void* out,
+                              int64_t ld_out, int64_t N, void* scratch, size_t scratch_bytes,
+                              cusadi_stream stream);
+
 }  // namespace cusadi

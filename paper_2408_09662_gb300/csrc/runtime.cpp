@@ -366,6 +366,52 @@ cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const 
 
 }  // namespace
 
+namespace cusadi {
+
+cusadi_status report(cusadi_status s, const std::string& msg) { return fail(s, msg); }
+
+// Forward evaluation with a caller-supplied scratch region used as the
+// workspace.  Loads nothing: the function's kernels must already be on the
+// current device.  Used by the allocation-free entry point.
+cusadi_status eval_in_scratch(cusadi_fn fn, const void* in, int64_t ld_in, void* out,
+                              int64_t ld_out, int64_t N, void* scratch, size_t scratch_bytes,
+                              cusadi_stream stream) {
+  if (!fn) return fail(CUSADI_E_INVALID_ARG, "fn is NULL");
+  if (N < 0) return fail(CUSADI_E_INVALID_ARG, "N must be >= 0");
+  if (N == 0 || fn->ir.nnz_out == 0) return CUSADI_OK;
+  if (N > ((int64_t)1 << 40)) return fail(CUSADI_E_INVALID_ARG, "N too large");
+  if (fn->ir.nnz_in > 0) {
+    if (!in) return fail(CUSADI_E_INVALID_ARG, "in is NULL");
+    int64_t need = all_bcast(fn->fwd.g, fn->ir.nnz_in) ? 1 : N;
+    if (ld_in < need) return fail(CUSADI_E_INVALID_ARG, "ld_in smaller than N");
+  }
+  if (!out) return fail(CUSADI_E_INVALID_ARG, "out is NULL");
+  if (ld_out < N) return fail(CUSADI_E_INVALID_ARG, "ld_out smaller than N");
+  const size_t need = direction_ws(fn, fn->fwd, N);
+  if (need > scratch_bytes)
+    return fail(CUSADI_E_INVALID_ARG,
+                "this evaluation needs " + std::to_string(need) + " bytes of scratch; the static "
+                "scratch region holds " + std::to_string(scratch_bytes) +
+                " bytes (evaluate fewer instances per call)");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(CUSADI_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+  DevState* ds = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(fn->dev_mu);
+    auto it = fn->dev.find(dev);
+    if (it != fn->dev.end() && it->second.fwd_ready) ds = &it->second;
+  }
+  if (!ds)
+    return fail(CUSADI_E_INVALID_ARG,
+                "the function's kernels are not loaded on this device yet: call cusadi_eval "
+                "once on it first (loading them allocates device memory)");
+  return run(fn, fn->fwd, *ds, false, in, ld_in, nullptr, 0, out, ld_out, N,
+             need > 0 ? scratch : nullptr, 0, 0, stream);
+}
+
+}  // namespace cusadi
+
 extern "C" {
 
 void cusadi_default_options(cusadi_options* o) {
