@@ -247,8 +247,10 @@ def srb_f(x, u, p=SRB):
 
 
 def srb_rollout_loss(x0, K, steps=50, p=SRB):
-    """sum over instances and t = 1..steps of ||x_t||^2, u = u_grav - K x held per RK4 step."""
-    x = np.array(x0, dtype=np.float64)
+    """sum over instances and t = 1..steps of ||x_t||^2, u = u_grav - K x held per RK4 step.
+    Complex inputs are carried through unchanged (every step is analytic), which
+    gives complex-step derivatives: d L / d K_ab = Im L(K + i h e_ab) / h."""
+    x = np.array(x0, dtype=np.result_type(x0, K, np.float64))
     ug = np.zeros((12, 1))
     ug[2::3] = p["mass"] * p["g"] / 4
     total = 0.0
@@ -260,5 +262,5 @@ def srb_rollout_loss(x0, K, steps=50, p=SRB):
         k3 = srb_f(x + 0.5 * dt * k2, u, p)
         k4 = srb_f(x + dt * k3, u, p)
         x = x + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
-        total += float(np.sum(x * x))
+        total = total + np.sum(x * x)
     return total, x

@@ -42,28 +42,51 @@ def test_rollout_loss_matches_numpy_model(prog64):
     x0, K = srb_inputs(64, seed=1)
     L, xT, _, _ = _grad(prog64, x0, K, 10)
     ref_L, ref_x = M.srb_rollout_loss(x0, K, STEPS)
-    assert abs(L - ref_L) <= 1e-11 * abs(ref_L)
+    assert abs(L - float(ref_L)) <= 1e-11 * abs(ref_L)
     np.testing.assert_allclose(xT, ref_x, rtol=1e-10, atol=1e-12)
 
 
 def test_rollout_gradient_matches_central_differences(prog64):
+    """Central differences, h = 1e-6, FP64.  Their own error is rounding of the
+    loss, ~eps * |L| / h per difference, so that is added to the tolerance."""
     N = 16
     x0, K = srb_inputs(N, seed=2)
-    _, _, gx, gK = _grad(prog64, x0, K, 10)
+    L, _, gx, gK = _grad(prog64, x0, K, 10)
     h = 1e-6
+    fd_noise = 10 * np.finfo(np.float64).eps * abs(L) / h
     rng = np.random.default_rng(3)
     for (a, b) in [tuple(rng.integers(12, size=2)) for _ in range(16)]:
         Kp, Km = K.copy(), K.copy()
         Kp[a, b] += h
         Km[a, b] -= h
         fd = (M.srb_rollout_loss(x0, Kp, STEPS)[0] - M.srb_rollout_loss(x0, Km, STEPS)[0]) / (2 * h)
-        assert abs(gK[a, b] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(gK))), (a, b, gK[a, b], fd)
+        assert abs(gK[a, b] - fd) <= 1e-6 * abs(fd) + fd_noise, (a, b, gK[a, b], fd)
     for k in range(12):
         xp, xm = x0.copy(), x0.copy()
         xp[k, 5] += h
         xm[k, 5] -= h
         fd = (M.srb_rollout_loss(xp, K, STEPS)[0] - M.srb_rollout_loss(xm, K, STEPS)[0]) / (2 * h)
-        assert abs(gx[k, 5] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(gx))), (k, gx[k, 5], fd)
+        assert abs(gx[k, 5] - fd) <= 1e-6 * abs(fd) + fd_noise, (k, gx[k, 5], fd)
+
+
+def test_rollout_gradient_matches_complex_step(prog64):
+    """Complex-step derivatives of the numpy model are exact to rounding, so the
+    reverse sweep must agree to ~1e-10 of the largest gradient entry."""
+    N = 8
+    x0, K = srb_inputs(N, seed=8)
+    _, _, gx, gK = _grad(prog64, x0, K, 10)
+    h = 1e-30
+    rng = np.random.default_rng(9)
+    for (a, b) in [tuple(rng.integers(12, size=2)) for _ in range(12)]:
+        Kc = K.astype(np.complex128)
+        Kc[a, b] += 1j * h
+        cs = M.srb_rollout_loss(x0, Kc, STEPS)[0].imag / h
+        assert abs(gK[a, b] - cs) <= 1e-10 * np.max(np.abs(gK)), (a, b, gK[a, b], cs)
+    for k in range(0, 12, 3):
+        xc = x0.astype(np.complex128)
+        xc[k, 3] += 1j * h
+        cs = M.srb_rollout_loss(xc, K, STEPS)[0].imag / h
+        assert abs(gx[k, 3] - cs) <= 1e-10 * np.max(np.abs(gx)), (k, gx[k, 3], cs)
 
 
 def test_step_adjoint_matches_oracle_reverse_sweep(prog64):
