@@ -117,6 +117,117 @@ def cpu_oracle_baseline(ir: bytes, x: np.ndarray, sample: int):
                       f"{dt:.2f} s wall"}
 
 
+def _events_ms(fn, reps, flush):
+    """Median device time of fn() over reps calls (CUDA events on the current stream)."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+    return statistics.median(ts)
+
+
+def other_configs(dev, pk64, pk32, flush, reps):
+    """Live measurements of the other workloads (cart-pole, MPC, rollout, batch)."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import Oracle, tolerance
+    from paper_2408_09662_gb300 import inputs, peaks, programs
+    from paper_2408_09662_gb300.api import Batch, Function
+    from paper_2408_09662_gb300.rollout import StepProgram, rollout
+
+    out = {}
+    pk = {"f64": pk64, "f32": pk32, "mixed": pk32}
+
+    def frac(fn, N, ms, dt):
+        w = peaks.weighted_ops(fn.op_counts(), pk[dt]["weights"])
+        return w * N / (ms * 1e-3) / pk[dt]["fma_per_s"]
+
+    # --- C1 cart-pole RK4 + Jacobian, FP64 ---
+    c1 = Function(programs.cartpole_rk4(), dtype="f64")
+    rec = {"ops_live": int(c1.info.n_ops)}
+    for N in (4096, 65536):
+        x = torch.tensor(inputs.cartpole(N, seed=0), device=dev)
+        y = c1(x)
+        ms = _events_ms(lambda: c1(x, out=y), reps, flush)
+        rec[f"N{N}"] = {"ms": ms, "instance_evals_per_s": N / (ms * 1e-3),
+                        "roofline_frac_f64": frac(c1, N, ms, "f64")}
+    out["cartpole_rk4_jacobian_f64"] = rec
+
+    # --- C3 closed-form MPC, N = 16384, all-FP64 vs mixed (FP32 bulk, FP64 pivots) ---
+    ir3 = programs.quadrotor_mpc().to_bytes()
+    with ThreadPoolExecutor(2) as ex:
+        f3 = dict(zip(("f64", "mixed"), ex.map(lambda d: Function(ir3, dtype=d), ("f64", "mixed"))))
+    N = 16384
+    rng = np.random.default_rng(0)
+    X = np.vstack([rng.uniform(-0.5, 0.5, (6, N)), rng.uniform(-1, 1, (2, N))])
+    rec = {"ops_live": int(f3["f64"].info.n_ops), "N": N, "kernels": int(f3["f64"].info.n_segments)}
+    idx = rng.choice(N, 64, replace=False)
+    orc = Oracle(ir3)
+    for dt, fn in f3.items():
+        Xd = X if dt == "f64" else X.astype(np.float32).astype(np.float64)
+        x = torch.tensor(Xd, dtype=fn.torch_dtype, device=dev)
+        y = fn(x)
+        ms = _events_ms(lambda: fn(x, out=y), reps, flush)
+        ref = orc.eval(Xd[:, idx])
+        err = np.abs(y.double().cpu().numpy()[:, idx] - ref) / np.max(np.abs(ref), axis=1, keepdims=True)
+        rec[dt] = {"ms": ms, "instance_evals_per_s": N / (ms * 1e-3),
+                   "roofline_frac": frac(fn, N, ms, dt), "max_rel_err_vs_fp64_oracle": float(err.max())}
+    rec["mixed_speedup_vs_f64"] = rec["f64"]["ms"] / rec["mixed"]["ms"]
+    out["quadrotor_mpc"] = rec
+
+    # --- C4 differentiable rollout: 50 RK4 steps, N = 4096, forward and reverse ---
+    rec = {"N": 4096, "steps": 50, "checkpoint_every": 10}
+    rng = np.random.default_rng(0)
+    x0n, Kn = rng.uniform(-0.1, 0.1, (12, 4096)), rng.normal(0, 0.1, (12, 12))
+    for dt in ("f64", "f32"):
+        prog = StepProgram(Function(programs.srb_step(), dtype=dt, adjoint=1), 144, 12)
+        tdt = prog.fn.torch_dtype
+        x0 = torch.tensor(x0n, dtype=tdt, device=dev, requires_grad=True)
+        K = torch.tensor(Kn.reshape(144), dtype=tdt, device=dev, requires_grad=True)
+        L, _ = rollout(prog, x0, K, 50)
+        L.backward()
+        torch.cuda.synchronize()
+        fwd = _events_ms(lambda: rollout(prog, x0.detach(), K.detach(), 50), reps, flush)
+
+        def fb():
+            L, _ = rollout(prog, x0, K, 50)
+            L.backward()
+        both = _events_ms(fb, reps, flush)
+        rec[dt] = {"forward_ms": fwd, "backward_ms": both - fwd,
+                   "adjoint_forward_ratio": (both - fwd) / fwd,
+                   "step_ops": int(prog.fn.info.n_ops),
+                   "adjoint_ops": int(sum(prog.fn.op_counts(adjoint=True)))}
+    out["srb_rollout"] = rec
+
+    # --- C5 uneven batch: 8 random programs, one persistent graph launch vs 8 launches ---
+    sizes = [(1000, 65536), (5000, 32768), (10000, 32768), (20000, 16384), (50000, 8192),
+             (100000, 4096), (150000, 2048), (200000, 512)]
+    t0 = time.perf_counter()
+    irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(sizes)]
+    b = Batch(irs, [N for _, N in sizes], dtype="f32")
+    t_compile = time.perf_counter() - t0
+    xs = [torch.tensor(inputs.normal(64, N, seed=200 + j), dtype=torch.float32, device=dev)
+          for j, (_, N) in enumerate(sizes)]
+    outs = [torch.empty((32, N), dtype=torch.float32, device=dev) for _, N in sizes]
+    block = b.tune(xs, outs, reps=3)
+    ms_p = _events_ms(lambda: b(xs, outs, mode="persistent"), reps, flush)
+    ms_s = _events_ms(lambda: b(xs, outs, mode="plain"), reps, flush)
+    gen_ops = sum(n * N for n, N in sizes)
+    out["uneven_batch_f32"] = {
+        "programs": [{"ops_generated": n, "N": N} for n, N in sizes],
+        "op_instances_generated": gen_ops, "persistent_ms": ms_p, "plain_8_launches_ms": ms_s,
+        "speedup_persistent_vs_plain": ms_s / ms_p, "tile_block": block, **b.info(),
+        "gop_per_s_generated": gen_ops / (ms_p * 1e-3) * 1e-9, "setup_seconds": t_compile}
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm, on this host's cores."""
     from oracle import Oracle
@@ -157,6 +268,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true",
                     help="reuse peaks measured earlier on this machine (_build/peaks.json)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the cart-pole / MPC / rollout / batch measurements")
     ap.add_argument("--only", choices=["both", "f64", "f32"], default="both",
                     help="time one kernel only (for profiling); prints no JSON line")
     args = ap.parse_args()
@@ -240,8 +353,9 @@ def main():
     clocks = clk.summary()
 
     # ---- FP32 kernel, same protocol ----------------------------------------------
-    ev32 = timed(fn32, x32, y32, args.steps)
-    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk32:
+        ev32 = timed(fn32, x32, y32, args.steps)
+        torch.cuda.synchronize()
     ms32 = sum(s.elapsed_time(e) for s, e in ev32) / args.steps
 
     # ---- end to end through the public API: pinned host in, host out ------------
@@ -296,6 +410,9 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(ir, x_np, N_INST)
+    extra = None
+    if not args.no_configs:
+        extra = other_configs(dev, pk64, pk32, flush, reps=max(args.steps // 2, 5))
 
     line = {
         "metric": METRIC, "value": value, "unit": "instance-evals/s", "n_gpus": world,
@@ -318,7 +435,7 @@ def main():
                  "err_vs_fp64_oracle": {"max_rel_scaled": float(rel32.max()),
                                         "median_rel_scaled": float(np.median(rel32)),
                                         "frac_within_2e-4": float(np.mean(rel32 <= 2e-4))},
-                 "speedup_vs_fp64": t64 / t32},
+                 "speedup_vs_fp64": t64 / t32, "clocks": clk32.summary()},
         "f64_err_vs_oracle": {"max_rel_scaled": float(rel64.max()),
                               "frac_within_1e-12": float(np.mean(rel64 <= 1e-12))},
         "op_weights_f64": pk64["weights"], "op_weights_f32": pk32["weights"],
@@ -330,7 +447,10 @@ def main():
         "clocks": clocks,
         "cpu_baseline": cpu,
         "gpu": torch.cuda.get_device_name(dev),
+        "other_configs": extra,
     }
+    if extra is not None:
+        line["adjoint_forward_ratio"] = extra["srb_rollout"]["f64"]["adjoint_forward_ratio"]
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -190,6 +190,52 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
 cusadi_status cusadi_eval_noalloc(cusadi_fn fn, const void* in, int64_t ld_in, void* out,
                                   int64_t ld_out, int64_t N, cusadi_stream stream);
 
+/* ---- batched launch of several programs ------------------------------------
+ * CusADi puts all operations of a function into one kernel to save launch
+ * overhead (§III-A, end).  A batch carries that over to several functions of
+ * uneven size, each over its own fixed instance count: every program is
+ * compiled as relocatable one-instance device functions and linked (nvJitLink)
+ * with a persistent scheduler kernel.  Its CTAs repeatedly take the next tile
+ * (one program, `block` consecutive instances) from an atomic ticket; tiles are
+ * ordered longest program first, so the few-instance long programs start at
+ * once and the short ones fill the GPU around them.  The launch (ticket reset +
+ * kernel) is captured once per device in a CUDA graph and replayed.  The same
+ * link also has one plain kernel per program (CUSADI_BATCH_PLAIN), so the two
+ * modes run identical per-instance code and give bit-identical results. */
+#define CUSADI_BATCH_PERSISTENT 0  /* one graph launch of the scheduler kernel */
+#define CUSADI_BATCH_PLAIN 1       /* one kernel launch per program, in order */
+
+/* Compiles and links n programs (irs[j] of nbytes[j] bytes) for N[j]
+ * instances each.  opt: dtype, block (32, 64 or 128: instances per tile),
+ * maxrregcount, fmad, schedule, segment_ops, compile_threads, cache_dir;
+ * path and compile_limit_ops are ignored (always compiled).  n <= 32.
+ * Errors: INVALID_ARG, INVALID_IR, COMPILE, OOM. */
+cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, const int64_t* N,
+                                  int n, const cusadi_options* opt, cusadi_batch* out);
+void cusadi_batch_free(cusadi_batch b);
+
+/* Device workspace one evaluation needs (all programs' segment carries). */
+size_t cusadi_batch_workspace_bytes(cusadi_batch b);
+
+/* Evaluates every program: in[j] / out[j] are [nnz_in_j x ld_in[j]] and
+ * [nnz_out_j x ld_out[j]] device buffers (ld >= N[j]) as for cusadi_eval.
+ * mode: CUSADI_BATCH_PERSISTENT or CUSADI_BATCH_PLAIN.  The first call on a
+ * device loads the module, uploads the tile table and captures the graph
+ * (allocates; not capturable); later calls only copy the buffer table when
+ * it changed (a few hundred bytes) and launch. */
+cusadi_status cusadi_batch_eval(cusadi_batch b, const void* const* in, const int64_t* ld_in,
+                                void* const* out, const int64_t* ld_out, void* workspace,
+                                int mode, cusadi_stream stream);
+
+/* Selects the tile size (32, 64 or 128 instances = threads per CTA) of the
+ * persistent launch; the link holds all three. */
+cusadi_status cusadi_batch_set_block(cusadi_batch b, int block);
+
+/* Tile count, threads per CTA, persistent grid size (0 before the first
+ * evaluation on this device) and the linked kernel's registers per thread. */
+cusadi_status cusadi_batch_info(cusadi_batch b, int64_t* n_tiles, int32_t* block, int32_t* grid,
+                                int32_t* registers);
+
 /* Writes the generated CUDA source of kernel `segment` (adjoint = 1: of the
  * adjoint kernels) into buf (NUL-terminated, truncated to *len bytes); sets *len
  * to the full size + 1.  UNSUPPORTED on the interpreter path. */

@@ -30,6 +30,7 @@ CUSADI_ADJ_ACCUMULATE = 1
 CUSADI_ADJ_REDUCE_BROADCAST = 2
 CUSADI_ADJ_ACCUMULATE_BROADCAST = 4
 CUSADI_NOALLOC_SCRATCH_BYTES = 64 << 20
+CUSADI_BATCH_PERSISTENT, CUSADI_BATCH_PLAIN = 0, 1
 
 
 class cusadi_options(ctypes.Structure):
@@ -75,6 +76,17 @@ SIGNATURES = {
                                  c_int64, c_uint32, c_void_p, c_void_p]),
     "cusadi_eval_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p]),
     "cusadi_source": (c_int32, [c_void_p, ctypes.c_int, ctypes.c_int, c_char_p, ctypes.POINTER(c_size_t)]),
+    "cusadi_batch_create": (c_int32, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t),
+                                      ctypes.POINTER(c_int64), ctypes.c_int,
+                                      ctypes.POINTER(cusadi_options), ctypes.POINTER(c_void_p)]),
+    "cusadi_batch_free": (None, [c_void_p]),
+    "cusadi_batch_workspace_bytes": (c_size_t, [c_void_p]),
+    "cusadi_batch_set_block": (c_int32, [c_void_p, ctypes.c_int]),
+    "cusadi_batch_eval": (c_int32, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_int64),
+                                    ctypes.POINTER(c_void_p), ctypes.POINTER(c_int64), c_void_p,
+                                    ctypes.c_int, c_void_p]),
+    "cusadi_batch_info": (c_int32, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int32),
+                                    ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
     "cusadi_status_string": (c_char_p, [c_int32]),
     "cusadi_last_error": (c_char_p, []),
 }
@@ -167,3 +179,42 @@ def cusadi_source(fn: int, adjoint: bool = False, segment: int = 0) -> str:
     buf = ctypes.create_string_buffer(n.value)
     check(lib().cusadi_source(fn, int(adjoint), segment, buf, ctypes.byref(n)), "cusadi_source")
     return buf.value.decode()
+
+
+def cusadi_batch_create(irs: list, N: list, opt: cusadi_options | None = None) -> int:
+    n = len(irs)
+    bufs = [ctypes.create_string_buffer(bytes(b), len(b)) for b in irs]
+    ptrs = (c_void_p * n)(*[ctypes.cast(b, c_void_p) for b in bufs])
+    sizes = (c_size_t * n)(*[len(b) for b in irs])
+    ns = (c_int64 * n)(*N)
+    h = c_void_p()
+    check(lib().cusadi_batch_create(ptrs, sizes, ns, n, ctypes.byref(opt) if opt is not None else None,
+                                    ctypes.byref(h)), "cusadi_batch_create")
+    return h.value
+
+
+def cusadi_batch_free(b: int) -> None:
+    if b and _LIB is not None:
+        _LIB.cusadi_batch_free(b)
+
+
+def cusadi_batch_workspace_bytes(b: int) -> int:
+    return int(lib().cusadi_batch_workspace_bytes(b))
+
+
+def cusadi_batch_set_block(b: int, block: int) -> None:
+    check(lib().cusadi_batch_set_block(b, block), "cusadi_batch_set_block")
+
+
+def cusadi_batch_eval(b: int, ins: list, ld_in: list, outs: list, ld_out: list, workspace: int,
+                      mode: int, stream: int) -> None:
+    n = len(ins)
+    check(lib().cusadi_batch_eval(b, (c_void_p * n)(*ins), (c_int64 * n)(*ld_in), (c_void_p * n)(*outs),
+                                  (c_int64 * n)(*ld_out), workspace, mode, stream), "cusadi_batch_eval")
+
+
+def cusadi_batch_info(b: int) -> tuple:
+    nt, blk, grid, regs = c_int64(), c_int32(), c_int32(), c_int32()
+    check(lib().cusadi_batch_info(b, ctypes.byref(nt), ctypes.byref(blk), ctypes.byref(grid),
+                                  ctypes.byref(regs)), "cusadi_batch_info")
+    return nt.value, blk.value, grid.value, regs.value

@@ -159,3 +159,88 @@ class _Apply(torch.autograd.Function):
 def apply(fn: Function, x: torch.Tensor) -> torch.Tensor:
     """Differentiable evaluation (torch.autograd)."""
     return _Apply.apply(fn, x)
+
+
+class Batch:
+    """Several programs, each over its own fixed instance count, evaluated by one
+    persistent kernel replayed from a CUDA graph (mode "persistent") or by one
+    plain kernel per program (mode "plain"); both run the same per-instance code."""
+
+    MODES = {"persistent": L.CUSADI_BATCH_PERSISTENT, "plain": L.CUSADI_BATCH_PLAIN}
+
+    def __init__(self, programs, N, dtype: str = "f32", block: int = 128, cache_dir=DEFAULT_CACHE,
+                 **options):
+        self._b = None
+        opt = L.cusadi_default_options()
+        opt.dtype = DTYPES[dtype]
+        opt.block = block
+        for k, v in options.items():
+            if not hasattr(opt, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(opt, k, int(v))
+        self._cache = cache_dir.encode() if cache_dir else None
+        if cache_dir:
+            os.makedirs(cache_dir, exist_ok=True)
+        opt.cache_dir = self._cache
+        irs = [_program_bytes(p) for p in programs]
+        self.N = [int(n) for n in N]
+        self._b = L.cusadi_batch_create(irs, self.N, opt)
+        self.torch_dtype = torch.float64 if dtype == "f64" else torch.float32
+        self.block = block
+        self._ws = None
+
+    def __del__(self):
+        if getattr(self, "_b", None):
+            L.cusadi_batch_free(self._b)
+            self._b = None
+
+    def info(self) -> dict:
+        nt, blk, grid, regs = L.cusadi_batch_info(self._b)
+        return {"tiles": nt, "block": blk, "grid": grid, "registers": regs}
+
+    def set_block(self, block: int) -> None:
+        L.cusadi_batch_set_block(self._b, block)
+        self.block = block
+
+    def workspace(self, device) -> torch.Tensor | None:
+        nb = L.cusadi_batch_workspace_bytes(self._b)
+        if nb == 0:
+            return None
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb, dtype=torch.uint8, device=device)
+        return self._ws
+
+    def __call__(self, xs, outs, mode: str = "persistent"):
+        """xs[j]: [nnz_in_j, N_j], outs[j]: [nnz_out_j, N_j] CUDA tensors."""
+        for x, o, n in zip(xs, outs, self.N):
+            for t in (x, o):
+                if not t.is_cuda or t.dtype != self.torch_dtype or t.stride(1) != 1 or t.shape[1] != n:
+                    raise ValueError("batch buffers must be CUDA [rows, N_j] tensors of the batch dtype")
+        dev = xs[0].device
+        ws = self.workspace(dev)
+        L.cusadi_batch_eval(self._b, [x.data_ptr() for x in xs], [Function._ld(x) for x in xs],
+                            [o.data_ptr() for o in outs], [Function._ld(o) for o in outs],
+                            ws.data_ptr() if ws is not None else 0, self.MODES[mode],
+                            torch.cuda.current_stream(dev).cuda_stream)
+        return outs
+
+    def tune(self, xs, outs, reps: int = 5) -> int:
+        """Times the persistent launch at each tile size and keeps the fastest."""
+        best = None
+        for block in (32, 64, 128):
+            self.set_block(block)
+            self(xs, outs)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                self(xs, outs)
+                e.record()
+                e.synchronize()
+                ts.append(s.elapsed_time(e))
+            t = min(ts)
+            if best is None or t < best[0]:
+                best = (t, block)
+        self.set_block(best[1])
+        return best[1]

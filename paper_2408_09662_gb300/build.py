@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libcusadi.so")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-HOST_SRC = ["ir.cpp", "passes.cpp", "codegen.cpp", "interp.cpp", "runtime.cpp"]
+HOST_SRC = ["ir.cpp", "passes.cpp", "codegen.cpp", "interp.cpp", "runtime.cpp", "batch.cpp"]
 DEVICE_SRC = ["kernels.cu", "noalloc.cu"]
 
 
@@ -62,7 +62,7 @@ def build(force: bool = False) -> str:
         objs = list(ex.map(_compile, srcs))
     lib64 = os.path.join(CUDA, "lib64")
     tmp = LIB + ".tmp"
-    cmd = ["g++", "-shared", "-o", tmp, *objs, "-L", lib64, "-lcudart_static", "-lnvrtc",
+    cmd = ["g++", "-shared", "-o", tmp, *objs, "-L", lib64, "-lcudart_static", "-lnvrtc", "-lnvJitLink",
            "-lpthread", "-ldl", "-lrt", f"-Wl,-rpath,{lib64}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

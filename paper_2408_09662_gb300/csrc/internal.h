@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "cusadi.h"
 
 namespace cusadi {
@@ -132,6 +134,25 @@ int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, con
                   void* stream);
 // threads per block of the shared-memory interpreter (0: work vector too long)
 int interp_block(int64_t n_slots, int dtype);
+
+// runtime.cpp: NVRTC compile with the in-memory and on-disk content-hash cache
+bool compile_nvrtc(const std::string& src, const std::string& name,
+                   const std::vector<std::string>& opts, const char* cache_dir, std::string& cubin,
+                   std::string& log);
+
+// Driver-API entry points, fetched through the runtime so that the library
+// does not link libcuda (it must load on machines without a GPU driver).
+struct Driver {
+  CUresult (*moduleLoadData)(CUmodule*, const void*) = nullptr;
+  CUresult (*moduleGetFunction)(CUfunction*, CUmodule, const char*) = nullptr;
+  CUresult (*moduleUnload)(CUmodule) = nullptr;
+  CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                           unsigned, CUstream, void**, void**) = nullptr;
+  CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
+  CUresult (*funcGetAttribute)(int*, CUfunction_attribute, CUfunction) = nullptr;
+  bool ok = false;
+};
+const Driver& driver();
 
 // runtime.cpp: records msg as this thread's last error and returns s
 cusadi_status report(cusadi_status s, const std::string& msg);

@@ -43,6 +43,10 @@ uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
 std::mutex g_cache_mu;
 std::unordered_map<uint64_t, std::string> g_cubins;  // content hash -> cubin
 
+}  // namespace
+
+namespace cusadi {
+
 bool compile_nvrtc(const std::string& src, const std::string& name,
                    const std::vector<std::string>& opts, const char* cache_dir, std::string& cubin,
                    std::string& log) {
@@ -114,17 +118,6 @@ bool compile_nvrtc(const std::string& src, const std::string& name,
   return true;
 }
 
-// Driver-API entry points, fetched through the runtime so that the library
-// does not link libcuda (it must load on machines without a GPU driver).
-struct Driver {
-  CUresult (*moduleLoadData)(CUmodule*, const void*) = nullptr;
-  CUresult (*moduleGetFunction)(CUfunction*, CUmodule, const char*) = nullptr;
-  CUresult (*moduleUnload)(CUmodule) = nullptr;
-  CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
-                           unsigned, CUstream, void**, void**) = nullptr;
-  bool ok = false;
-};
-
 const Driver& driver() {
   static Driver d;
   static std::once_flag once;
@@ -138,10 +131,16 @@ const Driver& driver() {
     d.ok = get("cuModuleLoadData", (void**)&d.moduleLoadData) &&
            get("cuModuleGetFunction", (void**)&d.moduleGetFunction) &&
            get("cuModuleUnload", (void**)&d.moduleUnload) &&
-           get("cuLaunchKernel", (void**)&d.launchKernel);
+           get("cuLaunchKernel", (void**)&d.launchKernel) &&
+           get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&d.occupancy) &&
+           get("cuFuncGetAttribute", (void**)&d.funcGetAttribute);
   });
   return d;
 }
+
+}  // namespace cusadi
+
+namespace {
 
 struct DevState {
   bool fwd_ready = false, adj_ready = false;

@@ -207,3 +207,21 @@ def test_adjoint_source_generates_reduction_for_broadcast_inputs():
         assert counts[Op.COS] == 1
     finally:
         L.cusadi_free(fn)
+
+
+def test_batch_compiles_and_links_without_a_gpu():
+    irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, n in enumerate([400, 1500])]
+    o = _opt(dtype=L.CUSADI_F32, segment_ops=600)
+    b = L.cusadi_batch_create(irs, [1000, 65], o)
+    try:
+        n_tiles, block, grid, regs = L.cusadi_batch_info(b)
+        assert n_tiles == 8 + 1 and block == 128 and grid == 0
+        assert L.cusadi_batch_workspace_bytes(b) > 0
+        L.cusadi_batch_set_block(b, 32)
+        assert L.cusadi_batch_info(b)[:2] == (32 + 3, 32)
+        with pytest.raises(L.CusadiError):
+            L.cusadi_batch_set_block(b, 48)
+    finally:
+        L.cusadi_batch_free(b)
+    with pytest.raises(L.CusadiError):
+        L.cusadi_batch_create(irs, [1000, 0], o)
