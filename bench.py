@@ -143,11 +143,9 @@ def other_configs(dev, pk64, pk32, flush, reps):
     from paper_2408_09662_gb300.rollout import StepProgram, rollout
 
     out = {}
-    pk = {"f64": pk64, "f32": pk32, "mixed": pk32}
 
     def frac(fn, N, ms, dt):
-        w = peaks.weighted_ops(fn.op_counts(), pk[dt]["weights"])
-        return w * N / (ms * 1e-3) / pk[dt]["fma_per_s"]
+        return peaks.roofline_seconds(fn, pk64, pk32) * N / (ms * 1e-3)
 
     # --- C1 cart-pole RK4 + Jacobian, FP64 ---
     c1 = Function(programs.cartpole_rk4(), dtype="f64")

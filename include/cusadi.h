@@ -78,6 +78,9 @@ typedef struct {
   int32_t inline_math;        /* 1: inline transcendental functions (slow compile) (0) */
   int32_t adjoint;            /* 1: build the adjoint kernels at load; 0: at the first call
                                  that needs them (cusadi_adjoint and friends)   (0) */
+  int32_t own_math;           /* 1: FP32 sin/cos/exp use the engine's own inline
+                                 implementations (<= 2 ulp; measured slower than the
+                                 library's on the random 20k-op program), 0: library (0) */
   const char* cache_dir;      /* directory for compiled kernels, NULL = in-memory only */
 } cusadi_options;
 
@@ -135,9 +138,10 @@ cusadi_status cusadi_info(cusadi_fn fn, cusadi_fn_info* out);
 /* Description of input (is_output = 0) or output argument `index`. */
 cusadi_status cusadi_arg_info(cusadi_fn fn, int is_output, int index, cusadi_arg* out);
 
-/* counts[op] = number of ops with that IR op code evaluated per instance by the
- * forward kernels (adjoint = 1: by the adjoint kernels), for op < n. */
-cusadi_status cusadi_op_counts(cusadi_fn fn, int adjoint, int64_t* counts, int n);
+/* counts[op] = number of ops with that IR op code evaluated per instance, for
+ * op < n.  which: 0 forward kernels, 1 adjoint kernels, 2 / 3 the same but
+ * only ops tagged FP64 (those a MIXED function evaluates in double). */
+cusadi_status cusadi_op_counts(cusadi_fn fn, int which, int64_t* counts, int n);
 
 /* Bytes of device workspace one evaluation of N instances needs (0 when the
  * program fits in one kernel).  The caller allocates it, 256-byte aligned. */

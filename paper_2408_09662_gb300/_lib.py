@@ -37,7 +37,8 @@ class cusadi_options(ctypes.Structure):
     _fields_ = [("dtype", c_int32), ("path", c_int32), ("compile_limit_ops", c_int64),
                 ("segment_ops", c_int64), ("block", c_int32), ("maxrregcount", c_int32),
                 ("fmad", c_int32), ("compile_threads", c_int32), ("schedule", c_int32),
-                ("inline_math", c_int32), ("adjoint", c_int32), ("cache_dir", c_char_p)]
+                ("inline_math", c_int32), ("adjoint", c_int32), ("own_math", c_int32),
+                ("cache_dir", c_char_p)]
 
 
 class cusadi_fn_info(ctypes.Structure):
@@ -147,9 +148,10 @@ def cusadi_arg_info(fn: int, is_output: bool, index: int) -> cusadi_arg:
     return a
 
 
-def cusadi_op_counts(fn: int, adjoint: bool = False, n: int = 64) -> list:
+def cusadi_op_counts(fn: int, adjoint: bool = False, n: int = 64, f64_only: bool = False) -> list:
     buf = (c_int64 * n)()
-    check(lib().cusadi_op_counts(fn, int(adjoint), buf, n), "cusadi_op_counts")
+    check(lib().cusadi_op_counts(fn, int(adjoint) | (2 if f64_only else 0), buf, n),
+          "cusadi_op_counts")
     return list(buf)
 
 

@@ -75,8 +75,8 @@ class Function:
     def compiled(self) -> bool:
         return self.info.path == L.CUSADI_PATH_COMPILED
 
-    def op_counts(self, adjoint: bool = False) -> list:
-        return L.cusadi_op_counts(self._fn, adjoint)
+    def op_counts(self, adjoint: bool = False, f64_only: bool = False) -> list:
+        return L.cusadi_op_counts(self._fn, adjoint, f64_only=f64_only)
 
     def source(self, adjoint: bool = False, segment: int = 0) -> str:
         return L.cusadi_source(self._fn, adjoint, segment)

@@ -82,6 +82,7 @@ struct Gen {
   std::vector<int64_t> ws_slot;     // workspace row of values crossing a cut
   std::vector<std::vector<int64_t>> out_rows;  // per node: output rows it feeds
   std::set<std::pair<int, bool>> calls;        // (op, f64) of out-of-line math used
+  bool own_f32 = false;                        // own FP32 sin/cos/exp used
 
   Gen(const Graph& g_, const CodegenOptions& o_) : g(g_), o(o_) {}
 
@@ -101,6 +102,55 @@ std::string call_name(int op, bool f64, bool inl) {
   if (inl) return f64 ? m.d : m.f;
   return std::string("cs_") + m.d + (f64 ? "_d" : "_f");
 }
+
+// The engine's own single-precision sin, cos and exp (FP32 ops when the
+// library's are not inlined): Cody & Waite argument reduction with an FMA per
+// step and near-minimax polynomials; constants from csrc/gen_math_coeffs.py.
+// sin/cos take the fast path for |x| <= 128 * pi/2, where the 17-bit leading
+// parts of pi/2 make j * part exact; anything else (and inf/NaN) goes to the
+// library function.  Branch-free apart from that rare fallback.
+bool own_f32_math(int op) { return op == SIN || op == COS || op == EXP; }
+
+const char* kOwnMathF32 = R"(static __device__ __noinline__ float cs_sin_slow(float a) { return sinf(a); }
+static __device__ __noinline__ float cs_cos_slow(float a) { return cosf(a); }
+static __device__ __forceinline__ void cs_sincos_core(float x, float& s, float& c, int& q) {
+  const float j = rintf(x * 0x1.45f306p-1f);
+  float r = fmaf(-j, 0x1.922p+0f, x);
+  r = fmaf(-j, -0x1.2aefp-18f, r);
+  r = fmaf(-j, 0x1.68c234p-39f, r);
+  q = (int)j;
+  const float t = r * r;
+  s = fmaf(r * t, fmaf(t, fmaf(t, -0x1.9943ep-13f, 0x1.11073ap-7f), -0x1.555546p-3f), r);
+  c = fmaf(t, fmaf(t, fmaf(t, fmaf(t, 0x1.99169ep-16f, -0x1.6c07f2p-10f), 0x1.55553cp-5f), -0x1p-1f), 1.0f);
+}
+static __device__ __forceinline__ float cs_own_sin_f(float x) {
+  if (!(fabsf(x) <= 201.0f)) return cs_sin_slow(x);
+  float s, c; int q;
+  cs_sincos_core(x, s, c, q);
+  const float v = (q & 1) ? c : s;
+  return (q & 2) ? -v : v;
+}
+static __device__ __forceinline__ float cs_own_cos_f(float x) {
+  if (!(fabsf(x) <= 201.0f)) return cs_cos_slow(x);
+  float s, c; int q;
+  cs_sincos_core(x, s, c, q);
+  const float v = (q & 1) ? s : c;
+  return ((q + 1) & 2) ? -v : v;
+}
+static __device__ __forceinline__ float cs_own_exp_f(float x) {
+  const float xc = x < -104.0f ? -104.0f : (x > 89.0f ? 89.0f : x);
+  const float k = rintf(xc * 0x1.715476p+0f);
+  float r = fmaf(-k, 0x1.62e4p-1f, xc);
+  r = fmaf(-k, 0x1.7f7d1cp-20f, r);
+  float p = fmaf(r, 0x1.6a2448p-10f, 0x1.1239d4p-7f);
+  p = fmaf(r, p, 0x1.5558f2p-5f);
+  p = fmaf(r, p, 0x1.555492p-3f);
+  p = fmaf(r, p, 0x1.fffffcp-2f);
+  p = fmaf(r * r, p, r) + 1.0f;
+  const int ki = (int)k, k1 = ki >> 1, k2 = ki - k1;
+  return (p * __int_as_float((k1 + 127) << 23)) * __int_as_float((k2 + 127) << 23);
+}
+)";
 
 }  // namespace
 
@@ -168,6 +218,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     std::ostringstream body;
     std::vector<uint8_t> have(n, 0);   // leaf or ws value materialised in this segment
     G.calls.clear();
+    G.own_f32 = false;
     auto operand = [&](int32_t i, bool want_f64) -> std::string {
       const Node& x = g.nodes[i];
       bool f = G.node_f64(i);
@@ -253,7 +304,10 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
         case OR: e = "((" + A + " != " + Z + " || " + B + " != " + Z + ") ? " + One + " : " + Z + ")"; break;
         case SIGN: e = "(" + A + " > " + Z + " ? " + One + " : (" + A + " < " + Z + " ? -" + One + " : " + Z + "))"; break;
         default:
-          if (op_call(x.op)) {
+          if (!f && !o.inline_math && o.own_math && own_f32_math(x.op)) {
+            G.own_f32 = true;
+            e = std::string(x.op == SIN ? "cs_own_sin_f(" : (x.op == COS ? "cs_own_cos_f(" : "cs_own_exp_f(")) + A + ")";
+          } else if (op_call(x.op)) {
             G.calls.insert({x.op, f});
             e = call_name(x.op, f, o.inline_math) + "(" + A + (op_arity(x.op) == 2 ? ", " + B : "") + ")";
           } else {
@@ -270,6 +324,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     src << "// Generated straight-line kernel: segment " << s << " of " << nseg
         << (o.adjoint ? " (adjoint)" : "") << ", dtype "
         << (o.dtype == CUSADI_F64 ? "f64" : (o.dtype == CUSADI_F32 ? "f32" : "mixed")) << "\n";
+    if (G.own_f32) src << kOwnMathF32;
     if (!o.inline_math) {
       for (auto& c : G.calls) {
         MathFn m = math_name(c.first);

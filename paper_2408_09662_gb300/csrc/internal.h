@@ -79,7 +79,7 @@ Graph adjoint_graph(const Graph& g);
 std::vector<int64_t> last_uses(const Graph& g);
 int64_t max_live(const Graph& g);
 int64_t count_ops(const Graph& g);
-void op_histogram(const Graph& g, std::vector<int64_t>& h);
+void op_histogram(const Graph& g, std::vector<int64_t>& h, bool f64_only = false);
 
 // --- code generation -------------------------------------------------------
 struct Segment {
@@ -100,6 +100,7 @@ struct CodegenOptions {
   int block = 128;
   int64_t segment_ops = 40000;
   bool inline_math = false;
+  bool own_math = false;         // own FP32 sin/cos/exp instead of library calls
   bool adjoint = false;
   int64_t split = -1;            // input rows >= split come from the second buffer
   bool device_fn = false;        // emit relocatable __device__ functions of one instance

@@ -276,10 +276,10 @@ int64_t count_ops(const Graph& g) {
   return c;
 }
 
-void op_histogram(const Graph& g, std::vector<int64_t>& h) {
+void op_histogram(const Graph& g, std::vector<int64_t>& h, bool f64_only) {
   h.assign(N_OPS, 0);
   for (const Node& n : g.nodes)
-    if (n.op != INPUT && n.op != CONST) h[n.op]++;
+    if (n.op != INPUT && n.op != CONST && (!f64_only || n.f64)) h[n.op]++;
 }
 
 // ---------------------------------------------------------------------------

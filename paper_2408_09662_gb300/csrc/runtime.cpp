@@ -144,6 +144,7 @@ namespace {
 
 struct DevState {
   bool fwd_ready = false, adj_ready = false;
+  int sms = 0;                       // streaming multiprocessors of the device
   std::vector<CUmodule> mods;
   std::vector<CUfunction> fwd, adj;
   CUfunction adj_zero = nullptr;
@@ -157,7 +158,7 @@ struct DevState {
 struct Direction {
   Graph g;
   int64_t n_ops = 0, n_slots = 0;
-  std::vector<int64_t> hist;
+  std::vector<int64_t> hist, hist_f64;
   CodegenResult cg;
   std::vector<std::string> bins;
   InterpProgram ip;
@@ -197,6 +198,7 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.block = fn->opt.block;
   co.segment_ops = fn->opt.segment_ops;
   co.inline_math = fn->opt.inline_math != 0;
+  co.own_math = fn->opt.own_math != 0;
   co.adjoint = adjoint;
   co.split = adjoint ? fn->ir.nnz_in : -1;
   static const char* tag[] = {"f64", "f32", "mixed"};
@@ -234,6 +236,7 @@ cusadi_status prepare_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   d.n_ops = count_ops(d.g);
   d.n_slots = max_live(d.g);
   op_histogram(d.g, d.hist);
+  op_histogram(d.g, d.hist_f64, true);
   if (fn->path == CUSADI_PATH_INTERP) {
     std::string err;
     if (!pack_interp(d.g, d.ip, err)) return fail(CUSADI_E_UNSUPPORTED, err);
@@ -269,6 +272,11 @@ cusadi_status load_on_device(cusadi_fn fn, DevState& ds, bool adjoint) {
   cudaError_t ce = cudaFree(nullptr);  // makes the device's primary context current
   if (ce != cudaSuccess) return fail(CUSADI_E_CUDA, std::string("CUDA init: ") + cudaGetErrorString(ce));
   if (!driver().ok) return fail(CUSADI_E_CUDA, "CUDA driver entry points unavailable");
+  if (ds.sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ds.sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   Direction& d = adjoint ? fn->adj : fn->fwd;
   if (fn->path == CUSADI_PATH_INTERP) {
     void* ops = nullptr;
@@ -351,7 +359,11 @@ cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const 
     return CUSADI_OK;
   }
   const std::vector<CUfunction>& fs = adjoint ? ds.adj : ds.fwd;
-  const unsigned block = (unsigned)fn->opt.block;
+  // small batches: shrink the CTA (in warps) until every SM gets one, since a
+  // straight-line kernel's throughput per SM does not depend on how many CTAs
+  // share it but idle SMs are lost (N = 4096 at 128 threads fills 32 of 152)
+  unsigned block = (unsigned)fn->opt.block;
+  while (block > 32 && ds.sms > 0 && (N + block - 1) / block < ds.sms) block = (block / 2 + 31) / 32 * 32;
   const unsigned grid = (unsigned)((N + block - 1) / block);
   long long lx = ldx, lx2 = ldx2, ly = ldy, n = N, lw = round_up(N, 32);
   const void* x2 = X2 ? X2 : X;
@@ -426,6 +438,7 @@ void cusadi_default_options(cusadi_options* o) {
   o->schedule = 1;
   o->inline_math = 0;
   o->adjoint = 0;
+  o->own_math = 0;
   o->cache_dir = nullptr;
 }
 
@@ -548,13 +561,16 @@ cusadi_status cusadi_arg_info(cusadi_fn fn, int is_output, int index, cusadi_arg
   return CUSADI_OK;
 }
 
-cusadi_status cusadi_op_counts(cusadi_fn fn, int adjoint, int64_t* counts, int n) {
+cusadi_status cusadi_op_counts(cusadi_fn fn, int which, int64_t* counts, int n) {
   if (!fn || !counts || n < 0) return fail(CUSADI_E_INVALID_ARG, "NULL argument");
+  if (which < 0 || which > 3) return fail(CUSADI_E_INVALID_ARG, "which must be 0..3");
+  const bool adjoint = (which & 1) != 0, f64_only = (which & 2) != 0;
   if (adjoint) {
     cusadi_status s = ensure_adjoint(fn);
     if (s != CUSADI_OK) return s;
   }
-  const std::vector<int64_t>& h = adjoint ? fn->adj.hist : fn->fwd.hist;
+  const Direction& d = adjoint ? fn->adj : fn->fwd;
+  const std::vector<int64_t>& h = f64_only ? d.hist_f64 : d.hist;
   for (int i = 0; i < n; ++i) counts[i] = i < (int)h.size() ? h[i] : 0;
   return CUSADI_OK;
 }

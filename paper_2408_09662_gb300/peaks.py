@@ -131,3 +131,18 @@ def cached_or_measure(gpu_name: str, reuse: bool, path: str | None = None):
     with open(path, "w") as f:
         json.dump({"gpu": gpu_name, "f64": f64, "f32": f32}, f)
     return f64, f32
+
+
+def roofline_seconds(fn, f64_peaks: dict, f32_peaks: dict, adjoint: bool = False) -> float:
+    """Seconds per instance at the measured peaks: each op costs w(op)/peak of the
+    precision it runs in (a MIXED function splits its ops between the FP64 and
+    FP32 pipes by their tags)."""
+    counts = fn.op_counts(adjoint)
+    if fn.dtype == "f64":
+        return weighted_ops(counts, f64_peaks["weights"]) / f64_peaks["fma_per_s"]
+    if fn.dtype == "f32":
+        return weighted_ops(counts, f32_peaks["weights"]) / f32_peaks["fma_per_s"]
+    c64 = fn.op_counts(adjoint, f64_only=True)
+    c32 = [a - b for a, b in zip(counts, c64)]
+    return (weighted_ops(c64, f64_peaks["weights"]) / f64_peaks["fma_per_s"] +
+            weighted_ops(c32, f32_peaks["weights"]) / f32_peaks["fma_per_s"])
