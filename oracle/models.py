@@ -106,7 +106,7 @@ def pendulum_energy(th, om, g_over_l=9.81):
 # ---------------------------------------------------------------------------
 QUAD = dict(mass=1.0, inertia=0.01, arm=0.2, g=9.81, dt=0.02, T=10,
             q=(10.0, 10.0, 1.0, 1.0, 1.0, 1.0), r=0.1, u_max=15.0, mu0=0.1, mu_end=0.001,
-            M=5, delta=1e-9, tau=0.995)
+            M=5, delta=1e-9, tau=0.995, penalty_mu0=10.0, penalty_growth=10.0)
 
 
 def quad_step(x, u, p):
@@ -138,7 +138,7 @@ def quad_step_jac(x, u, p):
     return A, B
 
 
-def quad_kkt(x, u, x0bar, wp, mu, p):
+def quad_kkt(x, u, x0bar, wp, mu, p, penalty=False):
     """KKT matrix and right-hand side at (x, u): unknowns (dz, lambda)."""
     Tn = p["T"]
     nx, nu = 6 * (Tn + 1), 2 * Tn
@@ -154,6 +154,12 @@ def quad_kkt(x, u, x0bar, wp, mu, p):
     for k in range(Tn):
         for j in range(2):
             a = nx + 2 * k + j
+            if penalty:
+                # quadratic penalty of the bound violation, active set at u
+                over, under = max(u[k][j] - p["u_max"], 0.0), max(-u[k][j], 0.0)
+                H[a, a] = 2 * p["r"] + (2 * mu if (over > 0 or under > 0) else 0.0)
+                g[a] = 2 * p["r"] * (u[k][j] - uh) + 2 * mu * (over - under)
+                continue
             lo, hi = 1 / u[k][j], 1 / (p["u_max"] - u[k][j])
             H[a, a] = 2 * p["r"] + mu * (lo * lo + hi * hi)
             g[a] = 2 * p["r"] * (u[k][j] - uh) - mu * (lo - hi)
@@ -173,23 +179,31 @@ def quad_kkt(x, u, x0bar, wp, mu, p):
     return K, rhs
 
 
-def quadrotor_mpc(x0bar, wp, M=None, **over):
-    """z after M barrier-Newton iterations (the reading documented with the
-    program generator), with every KKT system solved densely by LAPACK."""
+def quadrotor_mpc(x0bar, wp, M=None, penalty=False, z_prev=None, **over):
+    """z after M Newton iterations (the reading documented with the program
+    generator), with every KKT system solved densely by LAPACK.  penalty: the
+    quadratic-penalty form with full steps; z_prev: warm start."""
     p = dict(QUAD)
     p.update(over)
     if M is not None:
         p["M"] = M
     Tn = p["T"]
-    uh = p["mass"] * p["g"] / 2
-    u = [np.array([uh, uh]) for _ in range(Tn)]
-    x = [np.asarray(x0bar, dtype=np.float64)]
-    for k in range(Tn):
-        x.append(quad_step(x[k], u[k], p))
     nx = 6 * (Tn + 1)
+    uh = p["mass"] * p["g"] / 2
+    if z_prev is not None:
+        x = [np.asarray(x0bar, dtype=np.float64)] + [np.array(z_prev[6 * k:6 * k + 6]) for k in range(1, Tn + 1)]
+        u = [np.array(z_prev[nx + 2 * k:nx + 2 * k + 2]) for k in range(Tn)]
+    else:
+        u = [np.array([uh, uh]) for _ in range(Tn)]
+        x = [np.asarray(x0bar, dtype=np.float64)]
+        for k in range(Tn):
+            x.append(quad_step(x[k], u[k], p))
     for it in range(p["M"]):
-        mu = p["mu0"] * (p["mu_end"] / p["mu0"]) ** (it / (p["M"] - 1)) if p["M"] > 1 else p["mu0"]
-        K, rhs = quad_kkt(x, u, x0bar, wp, mu, p)
+        if penalty:
+            mu = p["penalty_mu0"] * p["penalty_growth"] ** it
+        else:
+            mu = p["mu0"] * (p["mu_end"] / p["mu0"]) ** (it / (p["M"] - 1)) if p["M"] > 1 else p["mu0"]
+        K, rhs = quad_kkt(x, u, x0bar, wp, mu, p, penalty=penalty)
         s = np.linalg.solve(K, rhs)
         du = s[nx:nx + 2 * Tn].reshape(Tn, 2)
         dx = s[:nx].reshape(Tn + 1, 6)
@@ -197,7 +211,7 @@ def quadrotor_mpc(x0bar, wp, M=None, **over):
         with np.errstate(divide="ignore"):
             lo = np.where(du < 0, U / np.maximum(-du, 0), np.inf)
             hi = np.where(du > 0, (p["u_max"] - U) / np.maximum(du, 0), np.inf)
-        alpha = min(1.0, p["tau"] * float(np.min(np.minimum(lo, hi))))
+        alpha = 1.0 if penalty else min(1.0, p["tau"] * float(np.min(np.minimum(lo, hi))))
         x = [x[k] + alpha * dx[k] for k in range(Tn + 1)]
         u = [u[k] + alpha * du[k] for k in range(Tn)]
     return np.concatenate([np.concatenate(x), np.concatenate(u)])
@@ -264,3 +278,33 @@ def srb_rollout_loss(x0, K, steps=50, p=SRB):
         x = x + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
         total = total + np.sum(x * x)
     return total, x
+
+
+# ---------------------------------------------------------------------------
+# quadcopter LQR closed-loop step (infinite horizon, DARE by scipy)
+# ---------------------------------------------------------------------------
+def quad_hover_AB(mass, inertia, p=QUAD):
+    """Linearisation of the semi-implicit Euler step at hover (theta = 0, F = m g)."""
+    dt, g, arm = p["dt"], p["g"], p["arm"]
+    A = np.eye(6)
+    A[0, 3] = A[1, 4] = A[2, 5] = dt
+    A[3, 2] = -dt * g
+    A[0, 2] = dt * A[3, 2]
+    B = np.zeros((6, 2))
+    B[4, :] = dt / mass
+    B[5, :] = [dt * arm / inertia, -dt * arm / inertia]
+    B[0:3, :] = dt * B[3:6, :]
+    return A, B
+
+
+def quad_lqr_step(z, theta, p=QUAD):
+    """theta = (u_max, mass, inertia, q (6), r); returns (z_next, X, K)."""
+    import scipy.linalg as sl
+    u_max, mass, inertia = theta[0], theta[1], theta[2]
+    Q, R = np.diag(theta[3:9]), theta[9] * np.eye(2)
+    A, B = quad_hover_AB(mass, inertia, p)
+    X = sl.solve_discrete_are(A, B, Q, R)
+    K = np.linalg.solve(R + B.T @ X @ B, B.T @ X @ A)
+    u = np.clip(mass * p["g"] / 2 - K @ z, 0.0, u_max)
+    pp = dict(p, mass=mass, inertia=inertia)
+    return quad_step(z, u, pp), X, K

@@ -181,7 +181,7 @@ def random_program(n_ops: int = 20000, n_in: int = 64, n_out: int = 32,
 # ---------------------------------------------------------------------------
 QUADROTOR = dict(mass=1.0, inertia=0.01, arm=0.2, g=9.81, dt=0.02, T=10,
                  q=(10.0, 10.0, 1.0, 1.0, 1.0, 1.0), r=0.1, u_max=15.0, mu0=0.1, mu_end=0.001,
-                 M=5, delta=1e-9, tau=0.995)
+                 M=5, delta=1e-9, tau=0.995, penalty_mu0=10.0, penalty_growth=10.0)
 
 
 def quadrotor_step(x, u, p):
@@ -303,7 +303,8 @@ def ldlt_solve(K, rhs, g, tag_pivots: bool):
     return s
 
 
-def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool = False) -> ProgramIR:
+def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool = False,
+                  constraint: str = "barrier", warm_start: bool = False) -> ProgramIR:
     """Closed-form MPC (Eq. 8: M fixed solver iterations, no branches).
 
     Problem: states x_0..x_T, thrusts u_0..u_{T-1} of the planar quadrotor,
@@ -317,6 +318,13 @@ def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool =
     Initial guess: u = u_h and the rollout of u_h from x0bar.
     Inputs: x0bar (6), waypoint (2).  Output: z = (x_0..x_T, u_0..u_{T-1}).
     debug_first_step: output the first KKT solution (in kkt_order) instead.
+
+    constraint = "penalty" is the paper's own form (Eq. 9): the bounds enter the
+    cost as mu_i sum [max(0, u - u_max)^2 + max(0, -u)^2] with
+    mu_i = penalty_mu0 * penalty_growth^i; its Gauss-Newton model uses the
+    active set at the current iterate, and every step is taken in full.
+    warm_start (real-time iteration, §V-A): an extra input z_prev (86) is the
+    initial guess, with x_0 replaced by x0bar.
     """
     from contextlib import nullcontext
     p = dict(QUADROTOR)
@@ -330,16 +338,24 @@ def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool =
     umax = p["u_max"]
     f64 = g.fp64 if mixed_tags else nullcontext
     xref = [wp[0], wp[1], 0.0, 0.0, 0.0, 0.0]
-    u = [[uh, uh] for _ in range(Tn)]
-    x = [list(x0bar)]
-    for k in range(Tn):
-        x.append(quadrotor_step(x[k], u[k], p))
+    if warm_start:
+        zprev = g.symbols(6 * (Tn + 1) + 2 * Tn)
+        x = [list(x0bar)] + [zprev[6 * k:6 * k + 6] for k in range(1, Tn + 1)]
+        u = [zprev[6 * (Tn + 1) + 2 * k:6 * (Tn + 1) + 2 * k + 2] for k in range(Tn)]
+    else:
+        u = [[uh, uh] for _ in range(Tn)]
+        x = [list(x0bar)]
+        for k in range(Tn):
+            x.append(quadrotor_step(x[k], u[k], p))
     order = kkt_order(Tn)
     pos = {e: i for i, e in enumerate(order)}
     n = len(order)
     first = None
     for it in range(M):
-        mu = p["mu0"] * (p["mu_end"] / p["mu0"]) ** (it / (M - 1)) if M > 1 else p["mu0"]
+        if constraint == "penalty":
+            mu = p["penalty_mu0"] * p["penalty_growth"] ** it
+        else:
+            mu = p["mu0"] * (p["mu_end"] / p["mu0"]) ** (it / (M - 1)) if M > 1 else p["mu0"]
         K = [[0.0] * n for _ in range(n)]
         rhs = [0.0] * n
         for k in range(Tn + 1):
@@ -351,11 +367,17 @@ def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool =
             for j in range(2):
                 a = pos[("u", k, j)]
                 uk = u[k][j]
-                with f64():
-                    inv_lo = 1.0 / uk
-                    inv_hi = 1.0 / (umax - uk)
-                    hb = mu * (inv_lo * inv_lo + inv_hi * inv_hi)
-                    gb = mu * (inv_lo - inv_hi)
+                if constraint == "penalty":
+                    over, under = T.fmax(uk - umax, 0.0), T.fmax(-uk, 0.0)
+                    active = T.logical_or(0.0 < over, 0.0 < under)
+                    hb = 2.0 * mu * active
+                    gb = 2.0 * mu * (under - over)      # minus the penalty gradient
+                else:
+                    with f64():
+                        inv_lo = 1.0 / uk
+                        inv_hi = 1.0 / (umax - uk)
+                        hb = mu * (inv_lo * inv_lo + inv_hi * inv_hi)
+                        gb = mu * (inv_lo - inv_hi)
                 K[a][a] = 2.0 * p["r"] + hb
                 rhs[a] = -(2.0 * p["r"] * (uk - uh) - gb)
         # constraints: lam0 -> x0 - x0bar;  lam_{k+1} -> x_{k+1} - step(x_k, u_k)
@@ -386,18 +408,23 @@ def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool =
                 break
         dx = [[s[pos[("x", k, i)]] for i in range(6)] for k in range(Tn + 1)]
         du = [[s[pos[("u", k, j)]] for j in range(2)] for k in range(Tn)]
-        # fraction to the boundary of 0 < u < u_max, branch-free
-        ratio = None
-        for k in range(Tn):
-            for j in range(2):
-                lo = u[k][j] / T.fmax(-du[k][j], 0.0)
-                hi = (umax - u[k][j]) / T.fmax(du[k][j], 0.0)
-                r = T.fmin(lo, hi)
-                ratio = r if ratio is None else T.fmin(ratio, r)
-        alpha = T.fmin(1.0, p["tau"] * ratio)
+        if constraint == "penalty":
+            alpha = 1.0
+        else:
+            # fraction to the boundary of 0 < u < u_max, branch-free
+            ratio = None
+            for k in range(Tn):
+                for j in range(2):
+                    lo = u[k][j] / T.fmax(-du[k][j], 0.0)
+                    hi = (umax - u[k][j]) / T.fmax(du[k][j], 0.0)
+                    r = T.fmin(lo, hi)
+                    ratio = r if ratio is None else T.fmin(ratio, r)
+            alpha = T.fmin(1.0, p["tau"] * ratio)
         x = [[x[k][i] + alpha * dx[k][i] for i in range(6)] for k in range(Tn + 1)]
         u = [[u[k][j] + alpha * du[k][j] for j in range(2)] for k in range(Tn)]
     ins = [("x0", x0bar), ("waypoint", wp)]
+    if warm_start:
+        ins.append(("z_prev", zprev))
     if debug_first_step:
         return T.Function(ins, [("kkt_solution", first)]).to_ir()
     z = [v for k in range(Tn + 1) for v in x[k]] + [v for k in range(Tn) for v in u[k]]
@@ -471,3 +498,127 @@ def srb_step(params=None) -> ProgramIR:
     Ln = L + sum(v * v for v in xn)
     return T.Function([("K", K, ARG_BROADCAST), ("x", x), ("L", [L])],
                       [("x_next", xn), ("L_next", [Ln])]).to_ir()
+
+
+# ---------------------------------------------------------------------------
+# Quadcopter closed-loop step with an infinite-horizon LQR solved by a fixed
+# number of structured-doubling iterations (§V-C)
+# ---------------------------------------------------------------------------
+LQR_PARAMS = ("u_max", "mass", "inertia", "q_px", "q_pz", "q_th", "q_vx", "q_vz", "q_om", "r")
+
+
+def _mm(X, Y):
+    """Product of traced matrices (lists of lists); structural zeros stay floats."""
+    n, m, k = len(X), len(Y[0]), len(Y)
+    out = []
+    for i in range(n):
+        row = []
+        for j in range(m):
+            acc = 0.0
+            for l in range(k):
+                a, b = X[i][l], Y[l][j]
+                if (isinstance(a, float) and a == 0.0) or (isinstance(b, float) and b == 0.0):
+                    continue
+                acc = acc + a * b
+            row.append(acc)
+        out.append(row)
+    return out
+
+
+def _tr(X):
+    return [list(r) for r in zip(*X)]
+
+
+def _add(X, Y):
+    return [[a + b for a, b in zip(r, s)] for r, s in zip(X, Y)]
+
+
+def _lu_solve(W, Rhs):
+    """Solve W Y = Rhs by Gaussian elimination without pivoting (W = I + G H
+    with G, H positive semidefinite: its eigenvalues are >= 1)."""
+    n = len(W)
+    W = [list(r) for r in W]
+    Y = [list(r) for r in Rhs]
+    for j in range(n):
+        for i in range(j + 1, n):
+            if isinstance(W[i][j], float) and W[i][j] == 0.0:
+                continue
+            l = W[i][j] / W[j][j]
+            for c in range(j + 1, n):
+                W[i][c] = W[i][c] - l * W[j][c]
+            Y[i] = [a - l * b for a, b in zip(Y[i], Y[j])]
+    for j in reversed(range(n)):
+        Y[j] = [a / W[j][j] for a in Y[j]]
+        for i in range(j):
+            if isinstance(W[i][j], float) and W[i][j] == 0.0:
+                continue
+            Y[i] = [a - W[i][j] * b for a, b in zip(Y[i], Y[j])]
+    return Y
+
+
+def sda_dare(A, B, Q, Rinv, iters):
+    """Structured doubling for the DARE X = A'XA - A'XB(R + B'XB)^-1 B'XA + Q:
+    A0 = A, G0 = B R^-1 B', H0 = Q; with W = I + G H,
+    A+ = A W^-1 A, G+ = G + A W^-1 G A', H+ = H + A' H W^-1 A; H -> X
+    quadratically.  A fixed number of iterations (no convergence test)."""
+    n = len(A)
+    G = _mm(_mm(B, Rinv), _tr(B))
+    H = [list(r) for r in Q]
+    Ak = [list(r) for r in A]
+    I = [[1.0 if i == j else 0.0 for j in range(n)] for i in range(n)]
+    for _ in range(iters):
+        W = _add(I, _mm(G, H))
+        Y = _lu_solve(W, [a + g for a, g in zip(Ak, G)])   # [W^-1 A | W^-1 G]
+        YA = [r[:n] for r in Y]
+        YG = [r[n:] for r in Y]
+        A_next = _mm(Ak, YA)
+        G = _add(G, _mm(_mm(Ak, YG), _tr(Ak)))
+        H = _add(H, _mm(_mm(_tr(Ak), H), YA))
+        Ak = A_next
+    return H
+
+
+def quadrotor_lqr_step(sda_iters: int = 12, debug_riccati: bool = False) -> ProgramIR:
+    """z+ = step(z, clip(u_h - K z, 0, u_max)), K the infinite-horizon LQR gain of
+    the hover linearisation, recomputed from the per-instance parameters
+    theta = (u_max, mass, inertia, Q diagonal (6), r) with R = r I.
+    debug_riccati: output the Riccati solution X (row-major) and K instead."""
+    p = dict(QUADROTOR)
+    g = T.Graph()
+    z = g.symbols(6)
+    th = g.symbols(len(LQR_PARAMS))
+    prm = dict(zip(LQR_PARAMS, th))
+    dt, grav, arm = p["dt"], p["g"], p["arm"]
+    m, I = prm["mass"], prm["inertia"]
+    # hover linearisation of the semi-implicit Euler step (theta = 0, F = m g)
+    A = [[1.0 if i == j else 0.0 for j in range(6)] for i in range(6)]
+    A[3][2] = -dt * grav
+    A[0][2] = -dt * dt * grav
+    A[0][3] = A[1][4] = A[2][5] = dt
+    B = [[0.0, 0.0] for _ in range(6)]
+    dvz = dt / m
+    dom = dt * arm / I
+    B[4] = [dvz, dvz]
+    B[1] = [dt * dvz, dt * dvz]
+    B[5] = [dom, -dom]
+    B[2] = [dt * dom, -dt * dom]
+    Q = [[prm[LQR_PARAMS[3 + i]] if i == j else 0.0 for j in range(6)] for i in range(6)]
+    rinv = 1.0 / prm["r"]
+    X = sda_dare(A, B, Q, [[rinv, 0.0], [0.0, rinv]], sda_iters)
+    # K = (R + B'XB)^-1 B'XA
+    BtX = _mm(_tr(B), X)
+    S = _add([[prm["r"], 0.0], [0.0, prm["r"]]], _mm(BtX, B))
+    det = S[0][0] * S[1][1] - S[0][1] * S[1][0]
+    Sinv = [[S[1][1] / det, -S[0][1] / det], [-S[1][0] / det, S[0][0] / det]]
+    K = _mm(Sinv, _mm(BtX, A))
+    ins = [("z", z), ("theta", th)]
+    if debug_riccati:
+        return T.Function(ins, [("X", [X[i][j] for i in range(6) for j in range(6)]),
+                                ("K", [K[i][j] for i in range(2) for j in range(6)])]).to_ir()
+    uh = m * grav / 2.0
+    u = []
+    for i in range(2):
+        v = uh - sum(K[i][j] * z[j] for j in range(6))
+        u.append(T.fmin(T.fmax(v, 0.0), prm["u_max"]))
+    pp = dict(p, mass=m, inertia=I)
+    return T.Function(ins, [("z_next", quadrotor_step(z, u, pp))]).to_ir()

@@ -83,3 +83,23 @@ def test_mpc_interpreter_matches(mpc):
     orc = Oracle(mpc)
     ref = orc.eval(X)
     _check(y, ref, tolerance(orc, X, ref, 1e-12, kind=0))
+
+
+@pytest.mark.parametrize("kw", [dict(constraint="penalty"), dict(warm_start=True)],
+                         ids=["penalty", "warm_start"])
+def test_mpc_variants_parity(kw):
+    """The paper's quadratic-penalty form and the warm-started (real-time
+    iteration) form, FP64 on the GPU against the oracle."""
+    ir = programs.quadrotor_mpc({"u_max": 12.0}, **kw).to_bytes()
+    N = 4096
+    X = mpc_inputs(N, seed=5)
+    X[6:] *= 6.0
+    if kw.get("warm_start"):
+        z0 = Oracle(programs.quadrotor_mpc({"u_max": 12.0, "M": 2}).to_bytes()).eval(X)
+        X = np.vstack([X, z0])
+    fn = Function(ir, dtype="f64")
+    y = _run(fn, X)
+    orc = Oracle(ir)
+    idx = np.random.default_rng(6).choice(N, 64, replace=False)
+    ref = orc.eval(X[:, idx])
+    _check(y[:, idx], ref, tolerance(orc, X[:, idx], ref, 1e-12, kind=0))

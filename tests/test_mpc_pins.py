@@ -103,3 +103,55 @@ def test_mixed_precision_emulation_error_is_small(mpc):
     ym = orc.eval(X, mode=MODE_MIXED)
     scale = np.max(np.abs(y64), axis=1, keepdims=True)
     assert np.max(np.abs(ym - y64) / scale) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# the paper's own form (Eq. 9): quadratic penalty, growing mu, full steps;
+# real-time-iteration warm start
+# ---------------------------------------------------------------------------
+def tight_inputs(N, seed):
+    """Targets far away so the unconstrained thrusts leave [0, u_max]."""
+    rng = np.random.default_rng(seed)
+    X = np.vstack([rng.uniform(-0.5, 0.5, (6, N)), rng.uniform(-1, 1, (2, N))])
+    X[6:] *= 6.0
+    return X
+
+
+def test_penalty_program_matches_dense_restatement():
+    params = {"u_max": 12.0}
+    ir = programs.quadrotor_mpc(params, constraint="penalty").to_bytes()
+    X = tight_inputs(12, seed=6)
+    y = Oracle(ir).eval(X)
+    for i in range(12):
+        ref = M.quadrotor_mpc(X[:6, i], X[6:, i], penalty=True, u_max=12.0)
+        np.testing.assert_allclose(y[:, i], ref, rtol=0, atol=1e-10 * np.max(np.abs(ref)))
+
+
+def test_penalty_violation_shrinks_as_mu_grows():
+    """For large enough mu the penalised problem solves the constrained one
+    (Eq. 9's justification): the worst bound violation falls with each
+    iteration's tenfold larger mu."""
+    X = tight_inputs(16, seed=7)
+    viol = []
+    for Mi in (2, 3, 4, 5):
+        ir = programs.quadrotor_mpc({"u_max": 12.0, "M": Mi}, constraint="penalty").to_bytes()
+        u = Oracle(ir).eval(X)[66:]
+        viol.append(np.max(np.maximum(u - 12.0, 0) + np.maximum(-u, 0)))
+    assert viol[0] > 0.05
+    assert all(b < a for a, b in zip(viol, viol[1:]))
+    assert viol[-1] < 0.05 * viol[0]
+
+
+def test_warm_start_matches_dense_restatement_and_converges():
+    """Real-time iteration: one Newton step from the previous solution.  From a
+    converged solution the step barely moves it."""
+    # one step at the final barrier weight, from the 8-iteration solution
+    ir1 = programs.quadrotor_mpc({"M": 1, "mu0": 0.001}, warm_start=True).to_bytes()
+    X = mpc_inputs(8, seed=8)
+    z_full = np.stack([M.quadrotor_mpc(X[:6, i], X[6:, i], M=8) for i in range(8)], axis=1)
+    y = Oracle(ir1).eval(np.vstack([X, z_full]))
+    for i in range(8):
+        ref = M.quadrotor_mpc(X[:6, i], X[6:, i], M=1, z_prev=z_full[:, i], mu0=0.001)
+        np.testing.assert_allclose(y[:, i], ref, rtol=0, atol=1e-10 * np.max(np.abs(ref)))
+    cold = Oracle(programs.quadrotor_mpc({"M": 1, "mu0": 0.001}).to_bytes()).eval(X)
+    assert np.max(np.abs(y - z_full)) < 0.01 * np.max(np.abs(cold - z_full))
