@@ -622,3 +622,28 @@ def quadrotor_lqr_step(sda_iters: int = 12, debug_riccati: bool = False) -> Prog
         u.append(T.fmin(T.fmax(v, 0.0), prm["u_max"]))
     pp = dict(p, mass=m, inertia=I)
     return T.Function(ins, [("z_next", quadrotor_step(z, u, pp))]).to_ir()
+
+
+# ---------------------------------------------------------------------------
+# §IV benchmark family: LDL^T solution of a symmetric positive definite system
+# ---------------------------------------------------------------------------
+def ldlt_spd_solve(n: int) -> ProgramIR:
+    """x = A^-1 b for a dense SPD A (lower triangle row-major, n(n+1)/2 inputs)
+    and b (n), by an unrolled LDL^T factorisation and two triangular solves.
+    §IV benchmarks five such functions, each with about ten times the
+    operations of the previous one (n = 5, 10, 22, 47, 100 here)."""
+    g = T.Graph()
+    low = g.symbols(n * (n + 1) // 2)
+    b = g.symbols(n)
+    K = [[0.0] * n for _ in range(n)]
+    t = 0
+    for i in range(n):
+        for j in range(i + 1):
+            K[i][j] = K[j][i] = low[t]
+            t += 1
+    x = ldlt_solve(K, list(b), g, tag_pivots=False)
+    lower = Sparsity.from_mask([[j <= i for j in range(n)] for i in range(n)])
+    return T.Function([("A", low, 0, lower), ("b", b)], [("x", x)]).to_ir()
+
+
+LDLT_SIZES = (5, 10, 22, 47, 100)

@@ -376,7 +376,9 @@ def jacobian(ys, xs):
 class Function:
     """A traced function: input arguments (lists of input Syms) -> output arguments.
 
-    ``inputs``  list of (name, [Sym...]) or (name, [Sym...], flags)
+    ``inputs``  list of (name, [Sym...]) or (name, [Sym...], flags) or
+                (name, [Sym...], flags, Sparsity): the Syms are the argument's
+                non-zeros in the pattern's storage order (default: a dense column)
     ``outputs`` list of (name, values, Sparsity or None); values are Sym or
                 numbers.  With a Sparsity, values lists the non-zeros in its
                 storage order; without one the output is a dense column.
@@ -384,10 +386,18 @@ class Function:
 
     def __init__(self, inputs, outputs):
         self.inputs = []
+        self.in_sparsity = []
         for spec in inputs:
             name, syms = spec[0], list(spec[1])
             flags = spec[2] if len(spec) > 2 else 0
+            sp = spec[3] if len(spec) > 3 and spec[3] is not None else None
+            if sp is None:
+                sp = Sparsity.dense(len(syms), 1, name, flags)
+            elif sp.nnz != len(syms):
+                raise ValueError(f"input {name}: {len(syms)} symbols for {sp.nnz} non-zeros")
+            sp.name, sp.flags = name, flags
             self.inputs.append((name, syms, flags))
+            self.in_sparsity.append(sp)
         self.outputs = []
         for spec in outputs:
             name, vals = spec[0], list(spec[1])
@@ -410,7 +420,7 @@ class Function:
 
     def to_ir(self) -> ProgramIR:
         g = self.g
-        in_specs = [Sparsity.dense(len(syms), 1, name, flags) for name, syms, flags in self.inputs]
+        in_specs = list(self.in_sparsity)
         out_specs = [sp for _, _, sp in self.outputs]
         input_index = {}
         gi = 0
