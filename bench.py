@@ -14,6 +14,7 @@ Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -33,6 +34,10 @@ N_INST = 65536
 N_OPS_GEN = 20000
 PROGRAM_SEED, INPUT_SEED = 0, 1
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch from an ncu capture of the generated
+# kernel with this source hash (profiles/cs_fwd_f64_random20k.md); a kernel
+# whose source changed since gets no traffic figure
+NCU_TRAFFIC = {"c26c9219142915d9": 26148096 + 463616}
 
 
 def workload_config(info=None):
@@ -420,7 +425,8 @@ def main():
         "gop_per_s": ops_live * N_INST / t64 * 1e-9,
         "roofline": {"bound": "alu", "achieved": ach64 * 1e-12, "peak": pk64["fma_per_s"] * 1e-12,
                      "unit": "TFMA/s (FMA-equivalent ops, FP64)", "frac": ach64 / pk64["fma_per_s"],
-                     "traffic": None,
+                     "traffic": NCU_TRAFFIC.get(hashlib.sha256(fn64.source().encode()).hexdigest()[:16]),
+                     "algorithmic_bytes": int((fn64.nnz_in + fn64.nnz_out) * 8 * N_INST),
                      "peak_source": "measured FP64 FMA-chain rate on this GPU (peaks.py)",
                      "work_per_instance_fma_eq": w64},
         "fp32": {"value": world * N_INST / t32, "unit": "instance-evals/s", "ms_per_step": ms32,
