@@ -61,7 +61,8 @@ typedef enum { CUSADI_F64 = 0, CUSADI_F32 = 1, CUSADI_MIXED = 2 } cusadi_dtype;
 /* Evaluation path.  COMPILED: generated straight-line CUDA kernels (one
  * instance per thread, values in registers).  INTERP: one precompiled kernel
  * that walks a packed instruction stream (no compile time; for programs too
- * large to compile).  AUTO picks COMPILED up to compile_limit_ops. */
+ * large to compile).  AUTO picks COMPILED up to compile_limit_ops, and the
+ * interpreter when the program is larger or NVRTC fails on it. */
 typedef enum { CUSADI_PATH_AUTO = 0, CUSADI_PATH_COMPILED = 1, CUSADI_PATH_INTERP = 2 } cusadi_path;
 
 typedef struct {
@@ -239,6 +240,12 @@ cusadi_status cusadi_batch_set_block(cusadi_batch b, int block);
  * evaluation on this device) and the linked kernel's registers per thread. */
 cusadi_status cusadi_batch_info(cusadi_batch b, int64_t* n_tiles, int32_t* block, int32_t* grid,
                                 int32_t* registers);
+
+/* Waits for all work queued on `stream` with a time limit: OK once it is done,
+ * TIMEOUT if it is still running after timeout_seconds (the work is left
+ * running; call again to keep waiting), CUDA if the stream reports an error.
+ * Polls; never blocks in the driver. */
+cusadi_status cusadi_stream_wait(cusadi_stream stream, double timeout_seconds);
 
 /* Writes the generated CUDA source of kernel `segment` (adjoint = 1: of the
  * adjoint kernels) into buf (NUL-terminated, truncated to *len bytes); sets *len

@@ -76,6 +76,7 @@ SIGNATURES = {
     "cusadi_adjoint": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                  c_int64, c_uint32, c_void_p, c_void_p]),
     "cusadi_eval_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p]),
+    "cusadi_stream_wait": (c_int32, [c_void_p, c_double]),
     "cusadi_source": (c_int32, [c_void_p, ctypes.c_int, ctypes.c_int, c_char_p, ctypes.POINTER(c_size_t)]),
     "cusadi_batch_create": (c_int32, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t),
                                       ctypes.POINTER(c_int64), ctypes.c_int,
@@ -173,6 +174,10 @@ def cusadi_adjoint(fn: int, inp: int, ld_in: int, out_bar: int, ld_ob: int, in_b
 def cusadi_eval_noalloc(fn: int, inp: int, ld_in: int, out: int, ld_out: int, N: int,
                         stream: int) -> None:
     check(lib().cusadi_eval_noalloc(fn, inp, ld_in, out, ld_out, N, stream), "cusadi_eval_noalloc")
+
+
+def cusadi_stream_wait(stream: int, timeout_seconds: float) -> None:
+    check(lib().cusadi_stream_wait(stream, timeout_seconds), "cusadi_stream_wait")
 
 
 def cusadi_source(fn: int, adjoint: bool = False, segment: int = 0) -> str:

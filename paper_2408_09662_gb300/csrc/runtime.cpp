@@ -12,6 +12,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -178,6 +179,7 @@ struct cusadi_fn_s {
   std::string adj_error;
   Direction adj;
   double compile_seconds = 0;
+  std::string compile_fallback;   // why AUTO fell back to the interpreter, if it did
   std::mutex dev_mu;
   std::map<int, DevState> dev;
 };
@@ -190,6 +192,13 @@ std::vector<std::string> nvrtc_options(const cusadi_options& o) {
   v.push_back(o.fmad ? "--fmad=true" : "--fmad=false");
   if (o.maxrregcount > 0) v.push_back("--maxrregcount=" + std::to_string(o.maxrregcount));
   return v;
+}
+
+// Host-side fault injection for tests: CUSADI_INJECT=compile makes every
+// NVRTC compile of this process fail (nothing on the GPU is involved).
+bool injected(const char* what) {
+  const char* e = std::getenv("CUSADI_INJECT");
+  return e && std::strstr(e, what) != nullptr;
 }
 
 cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
@@ -225,6 +234,7 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
     for (int t = 0; t < nt; ++t) th.emplace_back(work);
     for (auto& t : th) t.join();
   }
+  if (injected("compile")) return fail(CUSADI_E_COMPILE, "NVRTC failure injected (CUSADI_INJECT=compile)");
   for (size_t s = 0; s < ns; ++s)
     if (!ok[s]) return fail(CUSADI_E_COMPILE, "NVRTC failed on " + d.cg.segs[s].name + ": " + logs[s].substr(0, 4000));
   return CUSADI_OK;
@@ -237,13 +247,17 @@ cusadi_status prepare_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   d.n_slots = max_live(d.g);
   op_histogram(d.g, d.hist);
   op_histogram(d.g, d.hist_f64, true);
-  if (fn->path == CUSADI_PATH_INTERP) {
-    std::string err;
-    if (!pack_interp(d.g, d.ip, err)) return fail(CUSADI_E_UNSUPPORTED, err);
-    d.n_slots = d.ip.n_slots;
-    return CUSADI_OK;
+  if (fn->path == CUSADI_PATH_COMPILED) {
+    cusadi_status s = compile_direction(fn, d, adjoint);
+    // AUTO falls back to the interpreter kernel when the compiler fails
+    if (s != CUSADI_E_COMPILE || fn->opt.path != CUSADI_PATH_AUTO || adjoint) return s;
+    fn->compile_fallback = t_last_error;
+    fn->path = CUSADI_PATH_INTERP;
   }
-  return compile_direction(fn, d, adjoint);
+  std::string err;
+  if (!pack_interp(d.g, d.ip, err)) return fail(CUSADI_E_UNSUPPORTED, err);
+  d.n_slots = d.ip.n_slots;
+  return CUSADI_OK;
 }
 
 cusadi_status ensure_adjoint(cusadi_fn fn) {
@@ -651,6 +665,19 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
   }
   return run(fn, fn->adj, *ds, true, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, workspace, acc,
              reduce ? 1 : 0, stream);
+}
+
+cusadi_status cusadi_stream_wait(cusadi_stream stream, double timeout_seconds) {
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery((cudaStream_t)stream);
+    if (e == cudaSuccess) return CUSADI_OK;
+    if (e != cudaErrorNotReady) return fail(CUSADI_E_CUDA, std::string("cudaStreamQuery: ") + cudaGetErrorString(e));
+    double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (dt >= timeout_seconds)
+      return fail(CUSADI_E_TIMEOUT, "work on the stream still running after " + std::to_string(timeout_seconds) + " s");
+    std::this_thread::sleep_for(std::chrono::microseconds(dt < 1e-3 ? 10 : 200));
+  }
 }
 
 cusadi_status cusadi_source(cusadi_fn fn, int adjoint, int segment, char* buf, size_t* len) {

@@ -252,3 +252,20 @@ def test_autograd_through_function():
     ybar[:4] = 2 * yn[:4]
     ref = Oracle(ir).adjoint(x.detach().cpu().numpy(), ybar)
     np.testing.assert_allclose(g, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_stream_wait_times_out_then_completes():
+    """A bounded wait: a long evaluation is still running after 1 ms (TIMEOUT,
+    work left running), and a second wait with a generous limit sees it finish."""
+    from paper_2408_09662_gb300 import _lib as L
+    ir = programs.random_program(20000, seed=0).to_bytes()
+    fn = Function(ir, dtype="f64")
+    x = torch.tensor(inputs.normal(64, 65536, seed=1), device="cuda")
+    y = fn(x)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream().cuda_stream
+    fn(x, out=y)
+    with pytest.raises(L.CusadiError) as e:
+        L.cusadi_stream_wait(s, 0.001)
+    assert e.value.status == L.CUSADI_E_TIMEOUT
+    L.cusadi_stream_wait(s, 60.0)

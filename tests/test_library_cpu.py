@@ -225,3 +225,28 @@ def test_batch_compiles_and_links_without_a_gpu():
         L.cusadi_batch_free(b)
     with pytest.raises(L.CusadiError):
         L.cusadi_batch_create(irs, [1000, 0], o)
+
+
+def _run_with_env(code, **env):
+    import subprocess
+    import sys
+    e = dict(os.environ, **env)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=e, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    return r.stdout.strip()
+
+
+def test_injected_compile_failure_falls_back_to_the_interpreter_under_auto():
+    code = ("from paper_2408_09662_gb300 import _lib as L, programs as P\n"
+            "ir = P.cartpole_rk4().to_bytes()\n"
+            "o = L.cusadi_default_options()\n"
+            "fn = L.cusadi_load(ir, o)\n"
+            "print(L.cusadi_info(fn).path)\n"
+            "o.path = L.CUSADI_PATH_COMPILED\n"
+            "try:\n"
+            "    L.cusadi_load(ir, o)\n"
+            "    print('no error')\n"
+            "except L.CusadiError as e:\n"
+            "    print(e.status)\n")
+    out = _run_with_env(code, CUSADI_INJECT="compile").split()
+    assert out == [str(L.CUSADI_PATH_INTERP), str(L.CUSADI_E_COMPILE)]
