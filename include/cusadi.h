@@ -79,6 +79,10 @@ typedef struct {
   int32_t inline_math;        /* 1: inline transcendental functions (slow compile) (0) */
   int32_t adjoint;            /* 1: build the adjoint kernels at load; 0: at the first call
                                  that needs them (cusadi_adjoint and friends)   (0) */
+  int32_t ways;               /* >= 2: within-instance parallelism on the compiled forward
+                                 path: `ways` warps split each program across 32 instances
+                                 (latency-bound small batches, few-instance long programs);
+                                 0: one instance per thread                        (0) */
   int32_t own_math;           /* 1: FP32 sin/cos/exp use the engine's own inline
                                  implementations (<= 2 ulp; measured slower than the
                                  library's on the random 20k-op program), 0: library (0) */

@@ -37,7 +37,7 @@ class cusadi_options(ctypes.Structure):
     _fields_ = [("dtype", c_int32), ("path", c_int32), ("compile_limit_ops", c_int64),
                 ("segment_ops", c_int64), ("block", c_int32), ("maxrregcount", c_int32),
                 ("fmad", c_int32), ("compile_threads", c_int32), ("schedule", c_int32),
-                ("inline_math", c_int32), ("adjoint", c_int32), ("own_math", c_int32),
+                ("inline_math", c_int32), ("adjoint", c_int32), ("ways", c_int32), ("own_math", c_int32),
                 ("cache_dir", c_char_p)]
 
 

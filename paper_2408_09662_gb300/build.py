@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libcusadi.so")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-HOST_SRC = ["ir.cpp", "passes.cpp", "codegen.cpp", "interp.cpp", "runtime.cpp", "batch.cpp"]
+HOST_SRC = ["ir.cpp", "passes.cpp", "codegen.cpp", "coop.cpp", "interp.cpp", "runtime.cpp", "batch.cpp"]
 DEVICE_SRC = ["kernels.cu", "noalloc.cu"]
 
 

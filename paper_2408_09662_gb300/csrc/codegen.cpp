@@ -152,6 +152,48 @@ static __device__ __forceinline__ float cs_own_exp_f(float x) {
 }
 )";
 
+// C expression of one op with operand expressions A, B in precision f.
+std::string op_expr(Gen& G, const Node& x, bool f, const std::string& A, const std::string& B,
+                    const CodegenOptions& o) {
+  const char* T = G.ty(f);
+  std::string Z = std::string("(") + T + ")0", One = std::string("(") + T + ")1";
+  std::string e;
+  MathFn m = math_name(x.op);
+  const char* mn = f ? m.d : m.f;
+  switch (x.op) {
+    case ADD: e = A + " + " + B; break;
+    case SUB: e = A + " - " + B; break;
+    case MUL: e = A + " * " + B; break;
+    case DIV: e = A + " / " + B; break;
+    case NEG: e = "-" + A; break;
+    case SQ: e = A + " * " + A; break;
+    case INV: e = One + " / " + A; break;
+    case SQRT: case FABS: case FLOOR: case CEIL: e = std::string(mn) + "(" + A + ")"; break;
+    case FMIN: case FMAX: case COPYSIGN: e = std::string(mn) + "(" + A + ", " + B + ")"; break;
+    case FMA_CONST: e = std::string(f ? "fma(" : "fmaf(") + lit(x.k, f) + ", " + A + ", " + B + ")"; break;
+    case IF_ELSE_ZERO: e = "(" + A + " != " + Z + " ? " + B + " : " + Z + ")"; break;
+    case LT: e = "(" + A + " < " + B + " ? " + One + " : " + Z + ")"; break;
+    case LE: e = "(" + A + " <= " + B + " ? " + One + " : " + Z + ")"; break;
+    case EQ: e = "(" + A + " == " + B + " ? " + One + " : " + Z + ")"; break;
+    case NE: e = "(" + A + " != " + B + " ? " + One + " : " + Z + ")"; break;
+    case NOT: e = "(" + A + " == " + Z + " ? " + One + " : " + Z + ")"; break;
+    case AND: e = "((" + A + " != " + Z + " && " + B + " != " + Z + ") ? " + One + " : " + Z + ")"; break;
+    case OR: e = "((" + A + " != " + Z + " || " + B + " != " + Z + ") ? " + One + " : " + Z + ")"; break;
+    case SIGN: e = "(" + A + " > " + Z + " ? " + One + " : (" + A + " < " + Z + " ? -" + One + " : " + Z + "))"; break;
+    default:
+      if (!f && !o.inline_math && o.own_math && own_f32_math(x.op)) {
+        G.own_f32 = true;
+        e = std::string(x.op == SIN ? "cs_own_sin_f(" : (x.op == COS ? "cs_own_cos_f(" : "cs_own_exp_f(")) + A + ")";
+      } else if (op_call(x.op)) {
+        G.calls.insert({x.op, f});
+        e = call_name(x.op, f, o.inline_math) + "(" + A + (op_arity(x.op) == 2 ? ", " + B : "") + ")";
+      } else {
+        e = "/* unsupported op */ " + Z;
+      }
+  }
+  return e;
+}
+
 }  // namespace
 
 CodegenResult generate(const Graph& g, const CodegenOptions& o) {
@@ -279,41 +321,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
       const char* T = G.ty(f);
       std::string A = x.a >= 0 ? operand(x.a, f) : "";
       std::string B = x.b >= 0 ? operand(x.b, f) : "";
-      std::string Z = std::string("(") + T + ")0", One = std::string("(") + T + ")1";
-      std::string e;
-      MathFn m = math_name(x.op);
-      const char* mn = f ? m.d : m.f;
-      switch (x.op) {
-        case ADD: e = A + " + " + B; break;
-        case SUB: e = A + " - " + B; break;
-        case MUL: e = A + " * " + B; break;
-        case DIV: e = A + " / " + B; break;
-        case NEG: e = "-" + A; break;
-        case SQ: e = A + " * " + A; break;
-        case INV: e = One + " / " + A; break;
-        case SQRT: case FABS: case FLOOR: case CEIL: e = std::string(mn) + "(" + A + ")"; break;
-        case FMIN: case FMAX: case COPYSIGN: e = std::string(mn) + "(" + A + ", " + B + ")"; break;
-        case FMA_CONST: e = std::string(f ? "fma(" : "fmaf(") + lit(x.k, f) + ", " + A + ", " + B + ")"; break;
-        case IF_ELSE_ZERO: e = "(" + A + " != " + Z + " ? " + B + " : " + Z + ")"; break;
-        case LT: e = "(" + A + " < " + B + " ? " + One + " : " + Z + ")"; break;
-        case LE: e = "(" + A + " <= " + B + " ? " + One + " : " + Z + ")"; break;
-        case EQ: e = "(" + A + " == " + B + " ? " + One + " : " + Z + ")"; break;
-        case NE: e = "(" + A + " != " + B + " ? " + One + " : " + Z + ")"; break;
-        case NOT: e = "(" + A + " == " + Z + " ? " + One + " : " + Z + ")"; break;
-        case AND: e = "((" + A + " != " + Z + " && " + B + " != " + Z + ") ? " + One + " : " + Z + ")"; break;
-        case OR: e = "((" + A + " != " + Z + " || " + B + " != " + Z + ") ? " + One + " : " + Z + ")"; break;
-        case SIGN: e = "(" + A + " > " + Z + " ? " + One + " : (" + A + " < " + Z + " ? -" + One + " : " + Z + "))"; break;
-        default:
-          if (!f && !o.inline_math && o.own_math && own_f32_math(x.op)) {
-            G.own_f32 = true;
-            e = std::string(x.op == SIN ? "cs_own_sin_f(" : (x.op == COS ? "cs_own_cos_f(" : "cs_own_exp_f(")) + A + ")";
-          } else if (op_call(x.op)) {
-            G.calls.insert({x.op, f});
-            e = call_name(x.op, f, o.inline_math) + "(" + A + (op_arity(x.op) == 2 ? ", " + B : "") + ")";
-          } else {
-            e = "/* unsupported op */ " + Z;
-          }
-      }
+      std::string e = op_expr(G, x, f, A, B, o);
       body << "  const " << T << " v" << i << " = " << e << ";\n";
       if (G.ws_slot[i] >= 0)
         body << "  if (active) W[" << G.ws_slot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
@@ -394,6 +402,191 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     z << "}\n";
     R.segs[0].source += z.str();
   }
+  return R;
+}
+
+}  // namespace cusadi
+
+namespace cusadi {
+
+// Cooperative kernels: the CTA's warps split one program; lane l of every warp
+// works on instance 32 * blockIdx.x + l.  Each warp's code is one straight-line
+// region containing exactly n_phases - 1 barriers, so every warp reaches every
+// barrier; values read by another warp are staged in shared memory.
+CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopPlan& plan) {
+  CodegenResult R;
+  Gen G(g, o);
+  const int64_t n = (int64_t)g.nodes.size();
+  const int W = plan.ways;
+  G.out_rows.assign(n, {});
+  for (size_t r = 0; r < g.out.size(); ++r) G.out_rows[g.out[r]].push_back((int64_t)r);
+  // segments: runs of whole phases of at most ~segment_ops ops
+  std::vector<int64_t> ops_in_phase(plan.n_phases, 0);
+  for (int64_t i = 0; i < n; ++i)
+    if (!G.leaf(i)) ops_in_phase[plan.phase[i]]++;
+  std::vector<std::pair<int, int>> segs;  // [first phase, last phase + 1)
+  {
+    int start = 0;
+    int64_t acc = 0;
+    for (int q = 0; q < plan.n_phases; ++q) {
+      if (o.segment_ops > 0 && acc > 0 && acc + ops_in_phase[q] > o.segment_ops) {
+        segs.push_back({start, q});
+        start = q;
+        acc = 0;
+      }
+      acc += ops_in_phase[q];
+    }
+    segs.push_back({start, plan.n_phases});
+  }
+  const int nseg = (int)segs.size();
+  std::vector<int> seg_of_phase(plan.n_phases, 0);
+  for (int s = 0; s < nseg; ++s)
+    for (int q = segs[s].first; q < segs[s].second; ++q) seg_of_phase[q] = s;
+  G.seg_of.assign(n, -1);
+  G.last_seg.assign(n, -1);
+  for (int64_t i = 0; i < n; ++i)
+    if (!G.leaf(i)) G.seg_of[i] = seg_of_phase[plan.phase[i]];
+  for (int64_t i = 0; i < n; ++i) {
+    if (G.leaf(i)) continue;
+    const Node& x = g.nodes[i];
+    for (int32_t a : {x.a, x.b})
+      if (a >= 0 && !G.leaf(a)) G.last_seg[a] = std::max(G.last_seg[a], G.seg_of[i]);
+  }
+  // workspace rows for values crossing kernels (same interval reuse as generate)
+  G.ws_slot.assign(n, -1);
+  {
+    std::vector<std::vector<int64_t>> release(nseg + 1);
+    std::vector<int64_t> free_rows;
+    int64_t rows = 0;
+    std::vector<std::vector<int64_t>> defs(nseg);
+    for (int64_t i = 0; i < n; ++i)
+      if (!G.leaf(i)) defs[G.seg_of[i]].push_back(i);
+    for (int s = 0; s < nseg; ++s) {
+      if (s > 0) {
+        for (int64_t r : release[s - 1]) free_rows.push_back(r);
+        release[s - 1].clear();
+      }
+      for (int64_t i : defs[s]) {
+        if (G.last_seg[i] <= s) continue;
+        int64_t r;
+        if (!free_rows.empty()) { r = free_rows.back(); free_rows.pop_back(); }
+        else r = rows++;
+        G.ws_slot[i] = r;
+        release[G.last_seg[i]].push_back(r);
+      }
+    }
+    R.ws_rows = rows;
+  }
+  const char* tin = G.buf_f64() ? "double" : "float";
+  const char* tw = G.ws_f64() ? "double" : "float";
+  const bool sm_f64 = o.dtype != CUSADI_F32;  // shared slots hold the widest type in use
+  const char* tsm = sm_f64 ? "double" : "float";
+  // nodes per (segment, warp, phase) in topological order
+  for (int s = 0; s < nseg; ++s) {
+    std::vector<std::vector<std::vector<int64_t>>> work(W, std::vector<std::vector<int64_t>>(segs[s].second - segs[s].first));
+    for (int64_t i = 0; i < n; ++i)
+      if (!G.leaf(i) && G.seg_of[i] == s) work[plan.owner[i]][plan.phase[i] - segs[s].first].push_back(i);
+    std::ostringstream regions;
+    G.calls.clear();
+    G.own_f32 = false;
+    for (int w = 0; w < W; ++w) {
+      std::ostringstream body;
+      std::vector<uint8_t> have(n, 0);
+      auto operand = [&](int32_t i, bool want_f64) -> std::string {
+        const Node& x = g.nodes[i];
+        bool f = G.node_f64(i);
+        std::string name = "v" + std::to_string(i);
+        if (x.op == CONST) return lit(x.k, want_f64);
+        if (!have[i]) {
+          if (x.op == INPUT) {
+            body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")"
+                 << (x.bcast ? "Xb[" : "X[") << x.io << "ll * ldx];\n";
+          } else if (G.seg_of[i] != s) {
+            body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")W["
+                 << G.ws_slot[i] << "ll * ldw];\n";
+          } else if (plan.owner[i] != w) {
+            body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")cs_x["
+                 << plan.slot[i] << " * 32 + lane];\n";
+          }
+          have[i] = 1;
+        }
+        if (f != want_f64) return std::string("(") + G.ty(want_f64) + ")" + name;
+        return name;
+      };
+      const int nph = segs[s].second - segs[s].first;
+      for (int q = 0; q < nph; ++q) {
+        for (int64_t i : work[w][q]) {
+          const Node& x = g.nodes[i];
+          const bool f = G.node_f64((int32_t)i);
+          const char* T = G.ty(f);
+          std::string A = x.a >= 0 ? operand(x.a, f) : "";
+          std::string B = x.b >= 0 ? operand(x.b, f) : "";
+          body << "    const " << T << " v" << i << " = " << op_expr(G, x, f, A, B, o) << ";\n";
+          have[i] = 1;
+          if (plan.slot[i] >= 0) body << "    cs_x[" << plan.slot[i] << " * 32 + lane] = (" << tsm << ")v" << i << ";\n";
+          if (G.ws_slot[i] >= 0) body << "    if (active) W[" << G.ws_slot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
+          for (int64_t r : G.out_rows[i])
+            body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")v" << i << ";\n";
+        }
+        if (q + 1 < nph) body << "    cs_bar();\n";
+      }
+      if (s == 0 && w == 0) {
+        // outputs fed directly by inputs or constants
+        for (int64_t i = 0; i < n; ++i) {
+          if (!G.leaf(i) || G.out_rows[i].empty()) continue;
+          std::string v = operand((int32_t)i, G.node_f64((int32_t)i));
+          for (int64_t r : G.out_rows[i]) body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
+        }
+      }
+      regions << (w == 0 ? "  if (warp == 0) {\n" : "  } else if (warp == " + std::to_string(w) + ") {\n")
+              << body.str();
+    }
+    regions << "  }\n";
+    std::ostringstream src;
+    src << "// Generated cooperative kernel: segment " << s << " of " << nseg << ", " << W
+        << " warps per 32 instances, " << (segs[s].second - segs[s].first) << " phases\n";
+    if (G.own_f32) src << kOwnMathF32;
+    if (!o.inline_math) {
+      for (auto& c : G.calls) {
+        MathFn m = math_name(c.first);
+        const char* t = c.second ? "double" : "float";
+        bool bin = op_arity(c.first) == 2;
+        src << "static __device__ __noinline__ " << t << " " << call_name(c.first, c.second, false) << "("
+            << t << " a" << (bin ? std::string(", ") + t + " b" : "") << ") { return "
+            << (c.second ? m.d : m.f) << "(a" << (bin ? ", b" : "") << "); }\n";
+      }
+    }
+    // Barrier 1 over the whole CTA.  The warps reach it from different code
+    // (their own regions), so it must be the non-aligned form: barrier.sync
+    // without .aligned (bar.sync is the aligned one, defined only when every
+    // thread of the CTA executes the same barrier instruction).  Every warp
+    // executes the same number of them.
+    src << "static __device__ __forceinline__ void cs_bar() { asm volatile(\"barrier.sync 1, "
+        << 32 * W << ";\" ::: \"memory\"); }\n";
+    std::string name = o.prefix + "_" + std::to_string(s);
+    src << "extern \"C\" __global__ void __launch_bounds__(" << 32 * W << ") " << name << "(\n"
+        << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
+        << "* __restrict__ X2, long long ldx2, " << tin << "* __restrict__ Y, long long ldy,\n    long long N, "
+        << tw << "* __restrict__ W, long long ldw, int acc, int reduce) {\n"
+        << "  extern __shared__ __align__(16) unsigned char cs_smem[];\n"
+        << "  " << tsm << "* __restrict__ cs_x = reinterpret_cast<" << tsm << "*>(cs_smem);\n"
+        << "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n"
+        << "  const long long i0 = (long long)blockIdx.x * 32 + lane;\n"
+        << "  const bool active = i0 < N;\n"
+        << "  const long long i = active ? i0 : N - 1;\n"
+        << "  const " << tin << "* __restrict__ Xb = X;\n"
+        << "  X += i; Y += i; W += i;\n"
+        << "  (void)Xb; (void)X2; (void)ldx2; (void)W; (void)ldw; (void)acc; (void)reduce; (void)cs_x;\n"
+        << regions.str() << "}\n";
+    Segment S;
+    S.begin = segs[s].first;
+    S.end = segs[s].second;
+    S.name = name;
+    S.source = src.str();
+    R.segs.push_back(std::move(S));
+  }
+  R.coop_ways = W;
+  R.smem_bytes = (int64_t)std::max(plan.n_slots, 1) * 32 * (sm_f64 ? 8 : 4);
   return R;
 }
 

@@ -93,6 +93,8 @@ struct CodegenResult {
   int64_t ws_rows = 0;           // workspace rows (values carried between segments)
   bool has_reduce = false;
   std::string zero_kernel;       // name of the kernel that clears reduced rows
+  int coop_ways = 0;             // > 0: cooperative kernels, 32 * coop_ways threads per CTA
+  int64_t smem_bytes = 0;        // dynamic shared memory per CTA (cooperative kernels)
 };
 
 struct CodegenOptions {
@@ -108,6 +110,18 @@ struct CodegenOptions {
 };
 
 CodegenResult generate(const Graph& g, const CodegenOptions& o);
+
+// --- within-instance parallelism ----------------------------------------------
+struct CoopPlan {
+  int ways = 1;                  // warps cooperating on one group of 32 instances
+  std::vector<int> owner;        // per node: warp computing it (-1: input/constant)
+  std::vector<int> phase;        // per node: barrier-separated phase
+  std::vector<int> slot;         // per node: shared-memory slot if another warp reads it
+  int n_phases = 1, n_slots = 0;
+};
+CoopPlan plan_coop(const Graph& g, int ways, double comm_cost);
+// Kernels of W = ways warps per CTA, 32 instances per CTA (forward only).
+CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopPlan& plan);
 
 // --- interpreter stream -------------------------------------------------------
 // code = op | f64 << 7 | bcast << 6 ... packed per instruction (see kernels.cu)
@@ -151,6 +165,7 @@ struct Driver {
                            unsigned, CUstream, void**, void**) = nullptr;
   CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
   CUresult (*funcGetAttribute)(int*, CUfunction_attribute, CUfunction) = nullptr;
+  CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
   bool ok = false;
 };
 const Driver& driver();

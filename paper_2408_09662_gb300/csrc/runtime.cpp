@@ -134,7 +134,8 @@ const Driver& driver() {
            get("cuModuleUnload", (void**)&d.moduleUnload) &&
            get("cuLaunchKernel", (void**)&d.launchKernel) &&
            get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&d.occupancy) &&
-           get("cuFuncGetAttribute", (void**)&d.funcGetAttribute);
+           get("cuFuncGetAttribute", (void**)&d.funcGetAttribute) &&
+           get("cuFuncSetAttribute", (void**)&d.funcSetAttribute);
   });
   return d;
 }
@@ -212,7 +213,16 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.split = adjoint ? fn->ir.nnz_in : -1;
   static const char* tag[] = {"f64", "f32", "mixed"};
   co.prefix = std::string(adjoint ? "cs_adj_" : "cs_fwd_") + tag[fn->opt.dtype];
-  d.cg = generate(d.g, co);
+  if (fn->opt.ways > 1 && !adjoint) {
+    co.prefix = std::string("cs_coop") + std::to_string(fn->opt.ways) + "_" + tag[fn->opt.dtype];
+    CoopPlan plan = plan_coop(d.g, fn->opt.ways, 8.0);
+    d.cg = generate_coop(d.g, co, plan);
+    if (d.cg.smem_bytes > 200 * 1024)
+      return fail(CUSADI_E_UNSUPPORTED, "cooperative plan needs " + std::to_string(d.cg.smem_bytes) +
+                                            " bytes of shared memory; use fewer ways");
+  } else {
+    d.cg = generate(d.g, co);
+  }
   const size_t ns = d.cg.segs.size();
   d.bins.assign(ns, std::string());
   std::vector<std::string> logs(ns);
@@ -315,6 +325,10 @@ cusadi_status load_on_device(cusadi_fn fn, DevState& ds, bool adjoint) {
       CUfunction f;
       r = driver().moduleGetFunction(&f, m, d.cg.segs[s].name.c_str());
       if (r != CUDA_SUCCESS) return cuda_fail("cuModuleGetFunction", r);
+      if (d.cg.smem_bytes > 48 * 1024) {
+        r = driver().funcSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)d.cg.smem_bytes);
+        if (r != CUDA_SUCCESS) return cuda_fail("cuFuncSetAttribute", r);
+      }
       fs.push_back(f);
       if (s == 0 && adjoint && d.cg.has_reduce) {
         r = driver().moduleGetFunction(&ds.adj_zero, m, d.cg.zero_kernel.c_str());
@@ -378,12 +392,18 @@ cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const 
   // share it but idle SMs are lost (N = 4096 at 128 threads fills 32 of 152)
   unsigned block = (unsigned)fn->opt.block;
   while (block > 32 && ds.sms > 0 && (N + block - 1) / block < ds.sms) block = (block / 2 + 31) / 32 * 32;
-  const unsigned grid = (unsigned)((N + block - 1) / block);
+  unsigned grid = (unsigned)((N + block - 1) / block);
+  unsigned smem = 0;
+  if (d.cg.coop_ways > 0) {   // W warps per 32 instances
+    block = 32u * (unsigned)d.cg.coop_ways;
+    grid = (unsigned)((N + 31) / 32);
+    smem = (unsigned)d.cg.smem_bytes;
+  }
   long long lx = ldx, lx2 = ldx2, ly = ldy, n = N, lw = round_up(N, 32);
   const void* x2 = X2 ? X2 : X;
   for (size_t s = 0; s < fs.size(); ++s) {
     void* args[] = {(void*)&X, &lx, (void*)&x2, &lx2, &Y, &ly, &n, &W, &lw, &acc, &reduce};
-    CUresult r = driver().launchKernel(fs[s], grid, 1, 1, block, 1, 1, 0, (CUstream)stream, args, nullptr);
+    CUresult r = driver().launchKernel(fs[s], grid, 1, 1, block, 1, 1, smem, (CUstream)stream, args, nullptr);
     if (r != CUDA_SUCCESS) return cuda_fail("cuLaunchKernel", r);
   }
   return CUSADI_OK;
@@ -453,6 +473,7 @@ void cusadi_default_options(cusadi_options* o) {
   o->inline_math = 0;
   o->adjoint = 0;
   o->own_math = 0;
+  o->ways = 0;
   o->cache_dir = nullptr;
 }
 
@@ -492,6 +513,7 @@ cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* o
   if (o.block % 32 != 0 || o.block > 1024) return fail(CUSADI_E_INVALID_ARG, "block must be a multiple of 32 in [32, 1024]");
   if (o.maxrregcount < 0 || o.maxrregcount > 255) return fail(CUSADI_E_INVALID_ARG, "maxrregcount must be in [0, 255]");
   if (o.compile_limit_ops <= 0) o.compile_limit_ops = 300000;
+  if (o.ways < 0 || o.ways > 16 || o.ways == 1) return fail(CUSADI_E_INVALID_ARG, "ways must be 0 or 2..16");
   if (o.cache_dir) fn->cache_dir = o.cache_dir;
   o.cache_dir = nullptr;  // the caller's string is not kept
   auto t0 = std::chrono::steady_clock::now();

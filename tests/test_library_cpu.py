@@ -250,3 +250,31 @@ def test_injected_compile_failure_falls_back_to_the_interpreter_under_auto():
             "    print(e.status)\n")
     out = _run_with_env(code, CUSADI_INJECT="compile").split()
     assert out == [str(L.CUSADI_PATH_INTERP), str(L.CUSADI_E_COMPILE)]
+
+
+@pytest.mark.parametrize("ways", [2, 4, 8, 16])
+def test_cooperative_kernels_reach_every_barrier(ways):
+    """Each warp's region of a cooperative kernel holds the same number of
+    barriers (n_phases - 1), so no warp can wait on a barrier another warp
+    skips; the barrier's thread count equals the CTA size."""
+    import re as _re
+    for ir in (programs.cartpole_rk4(), programs.random_program(3000, seed=ways)):
+        fn = L.cusadi_load(ir.to_bytes(), _opt(ways=ways, segment_ops=1200))
+        try:
+            for seg in range(L.cusadi_info(fn).n_segments):
+                src = L.cusadi_source(fn, False, seg)
+                assert f"barrier.sync 1, {32 * ways};" in src and "bar.sync" not in src.replace("barrier.sync", "")
+                regions = _re.split(r"\n  (?:if|\} else if) \(warp == \d+\) \{\n", src)[1:]
+                assert len(regions) == ways
+                counts = {r.count("cs_bar();") for r in regions}
+                assert len(counts) == 1
+                assert "return" not in "".join(regions)
+        finally:
+            L.cusadi_free(fn)
+
+
+def test_cooperative_ways_validated():
+    with pytest.raises(L.CusadiError):
+        L.cusadi_load(programs.listing2().to_bytes(), _opt(ways=1))
+    with pytest.raises(L.CusadiError):
+        L.cusadi_load(programs.listing2().to_bytes(), _opt(ways=32))
