@@ -452,6 +452,11 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     for (int32_t a : {x.a, x.b})
       if (a >= 0 && !G.leaf(a)) G.last_seg[a] = std::max(G.last_seg[a], G.seg_of[i]);
   }
+  std::vector<int> slot, gslot;
+  int n_gslots = 0;
+  const bool sm64 = o.dtype != CUSADI_F32;
+  const int max_slots = (int)((160 * 1024) / (32 * (sm64 ? 8 : 4)));
+  const int n_slots = assign_coop_slots(g, plan, G.seg_of, max_slots, slot, gslot, n_gslots);
   // workspace rows for values crossing kernels (same interval reuse as generate)
   G.ws_slot.assign(n, -1);
   {
@@ -477,9 +482,12 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     }
     R.ws_rows = rows;
   }
+  // cross-warp values that did not fit in shared memory use rows after those
+  const int64_t g_base = R.ws_rows;
+  R.ws_rows += n_gslots;
   const char* tin = G.buf_f64() ? "double" : "float";
   const char* tw = G.ws_f64() ? "double" : "float";
-  const bool sm_f64 = o.dtype != CUSADI_F32;  // shared slots hold the widest type in use
+  const bool sm_f64 = sm64;  // shared slots hold the widest type in use
   const char* tsm = sm_f64 ? "double" : "float";
   // nodes per (segment, warp, phase) in topological order
   for (int s = 0; s < nseg; ++s) {
@@ -505,8 +513,12 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
             body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")W["
                  << G.ws_slot[i] << "ll * ldw];\n";
           } else if (plan.owner[i] != w) {
-            body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")cs_x["
-                 << plan.slot[i] << " * 32 + lane];\n";
+            if (slot[i] >= 0)
+              body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")cs_x["
+                   << slot[i] << " * 32 + lane];\n";
+            else
+              body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")W["
+                   << g_base + gslot[i] << "ll * ldw];\n";
           }
           have[i] = 1;
         }
@@ -523,7 +535,8 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
           std::string B = x.b >= 0 ? operand(x.b, f) : "";
           body << "    const " << T << " v" << i << " = " << op_expr(G, x, f, A, B, o) << ";\n";
           have[i] = 1;
-          if (plan.slot[i] >= 0) body << "    cs_x[" << plan.slot[i] << " * 32 + lane] = (" << tsm << ")v" << i << ";\n";
+          if (slot[i] >= 0) body << "    cs_x[" << slot[i] << " * 32 + lane] = (" << tsm << ")v" << i << ";\n";
+          if (gslot[i] >= 0) body << "    if (active) W[" << g_base + gslot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
           if (G.ws_slot[i] >= 0) body << "    if (active) W[" << G.ws_slot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
           for (int64_t r : G.out_rows[i])
             body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")v" << i << ";\n";
@@ -586,7 +599,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     R.segs.push_back(std::move(S));
   }
   R.coop_ways = W;
-  R.smem_bytes = (int64_t)std::max(plan.n_slots, 1) * 32 * (sm_f64 ? 8 : 4);
+  R.smem_bytes = (int64_t)std::max(n_slots, 1) * 32 * (sm_f64 ? 8 : 4);
   return R;
 }
 

@@ -37,7 +37,6 @@ CoopPlan plan_coop(const Graph& g, int ways, double comm_cost) {
   P.ways = ways;
   P.owner.assign(n, -1);
   P.phase.assign(n, 0);
-  P.slot.assign(n, -1);
   std::vector<double> finish(n, 0.0), avail(ways, 0.0);
   auto leaf = [&](int64_t i) { return g.nodes[i].op == INPUT || g.nodes[i].op == CONST; };
   for (int64_t i = 0; i < n; ++i) {
@@ -68,35 +67,57 @@ CoopPlan plan_coop(const Graph& g, int ways, double comm_cost) {
   P.n_phases = 1;
   for (int64_t i = 0; i < n; ++i)
     if (!leaf(i)) P.n_phases = std::max(P.n_phases, P.phase[i] + 1);
-  // values read by another warp get a shared-memory slot for the phases
-  // [producer phase, last cross-warp reader phase]
+  return P;
+}
+
+int assign_coop_slots(const Graph& g, const CoopPlan& P, const std::vector<int>& seg_of_node,
+                      int max_slots, std::vector<int>& slot, std::vector<int>& gslot,
+                      int& n_gslots) {
+  // Values read by another warp of the same kernel get a shared-memory slot for
+  // the phases [producer phase, last such reader's phase]; a slot is free again
+  // from the phase after its last reader.  When all max_slots are taken, the
+  // value goes to a workspace row instead (the CTA barrier orders global
+  // memory as well).  Reads from a later kernel go through the workspace.
+  const int64_t n = (int64_t)g.nodes.size();
+  auto leaf = [&](int64_t i) { return g.nodes[i].op == INPUT || g.nodes[i].op == CONST; };
+  slot.assign(n, -1);
+  gslot.assign(n, -1);
   std::vector<int> last_read(n, -1);
   for (int64_t i = 0; i < n; ++i) {
     if (leaf(i)) continue;
     const Node& x = g.nodes[i];
     for (int32_t o : {x.a, x.b})
-      if (o >= 0 && !leaf(o) && P.owner[o] != P.owner[i]) last_read[o] = std::max(last_read[o], P.phase[i]);
+      if (o >= 0 && !leaf(o) && P.owner[o] != P.owner[i] && seg_of_node[o] == seg_of_node[i])
+        last_read[o] = std::max(last_read[o], P.phase[i]);
   }
-  // outputs of ops are stored by their owner; only cross-warp reads need slots
   std::vector<std::vector<int64_t>> by_phase(P.n_phases);
   for (int64_t i = 0; i < n; ++i)
     if (last_read[i] >= 0) by_phase[P.phase[i]].push_back(i);
-  std::vector<std::vector<int>> release(P.n_phases + 1);
-  std::vector<int> free_slots;
+  std::vector<std::vector<int>> release(P.n_phases + 1), grelease(P.n_phases + 1);
+  std::vector<int> free_slots, free_g;
   int slots = 0;
+  n_gslots = 0;
   for (int q = 0; q < P.n_phases; ++q) {
-    // a slot whose last reader ran in phase q-1 or earlier is free from phase q on
     for (int s : release[q]) free_slots.push_back(s);
+    for (int s : grelease[q]) free_g.push_back(s);
     for (int64_t i : by_phase[q]) {
-      int s;
-      if (!free_slots.empty()) { s = free_slots.back(); free_slots.pop_back(); }
-      else s = slots++;
-      P.slot[i] = s;
-      release[std::min(last_read[i] + 1, P.n_phases)].push_back(s);
+      const int end = std::min(last_read[i] + 1, P.n_phases);
+      if (!free_slots.empty() || slots < max_slots) {
+        int s;
+        if (!free_slots.empty()) { s = free_slots.back(); free_slots.pop_back(); }
+        else s = slots++;
+        slot[i] = s;
+        release[end].push_back(s);
+      } else {
+        int s;
+        if (!free_g.empty()) { s = free_g.back(); free_g.pop_back(); }
+        else s = n_gslots++;
+        gslot[i] = s;
+        grelease[end].push_back(s);
+      }
     }
   }
-  P.n_slots = slots;
-  return P;
+  return slots;
 }
 
 }  // namespace cusadi

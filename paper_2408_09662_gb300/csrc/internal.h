@@ -116,10 +116,15 @@ struct CoopPlan {
   int ways = 1;                  // warps cooperating on one group of 32 instances
   std::vector<int> owner;        // per node: warp computing it (-1: input/constant)
   std::vector<int> phase;        // per node: barrier-separated phase
-  std::vector<int> slot;         // per node: shared-memory slot if another warp reads it
-  int n_phases = 1, n_slots = 0;
+  int n_phases = 1;
 };
 CoopPlan plan_coop(const Graph& g, int ways, double comm_cost);
+// Shared-memory slots (at most max_slots; overflow to workspace rows gslot) of
+// the values read by another warp of the same kernel (seg_of_node: kernel of
+// each node); returns the shared slot count.
+int assign_coop_slots(const Graph& g, const CoopPlan& P, const std::vector<int>& seg_of_node,
+                      int max_slots, std::vector<int>& slot, std::vector<int>& gslot,
+                      int& n_gslots);
 // Kernels of W = ways warps per CTA, 32 instances per CTA (forward only).
 CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopPlan& plan);
 

@@ -217,9 +217,8 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
     co.prefix = std::string("cs_coop") + std::to_string(fn->opt.ways) + "_" + tag[fn->opt.dtype];
     CoopPlan plan = plan_coop(d.g, fn->opt.ways, 8.0);
     d.cg = generate_coop(d.g, co, plan);
-    if (d.cg.smem_bytes > 200 * 1024)
-      return fail(CUSADI_E_UNSUPPORTED, "cooperative plan needs " + std::to_string(d.cg.smem_bytes) +
-                                            " bytes of shared memory; use fewer ways");
+    if (d.cg.smem_bytes > 200 * 1024)   // cannot happen: overflow goes to the workspace
+      return fail(CUSADI_E_UNSUPPORTED, "cooperative plan needs too much shared memory");
   } else {
     d.cg = generate(d.g, co);
   }
