@@ -11,6 +11,7 @@
 #include <cinttypes>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <set>
@@ -455,7 +456,15 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
   std::vector<int> slot, gslot;
   int n_gslots = 0;
   const bool sm64 = o.dtype != CUSADI_F32;
-  const int max_slots = (int)((160 * 1024) / (32 * (sm64 ? 8 : 4)));
+  // shared-memory budget for cross-warp values (CUSADI_COOP_SHARED_KB overrides
+  // it, so tests can force the workspace overflow path on small programs)
+  int budget_kb = 160;
+  if (const char* e = std::getenv("CUSADI_COOP_SHARED_KB")) budget_kb = std::max(0, std::atoi(e));
+  const int max_slots = (int)((budget_kb * 1024) / (32 * (sm64 ? 8 : 4)));
+  // CUSADI_COOP_REGIONS=1 selects per-warp regions with a non-aligned barrier
+  // instead of the phase-major layout with __syncthreads()
+  const char* reg_env = std::getenv("CUSADI_COOP_REGIONS");
+  const bool aligned = !(reg_env && reg_env[0] == '1');
   const int n_slots = assign_coop_slots(g, plan, G.seg_of, max_slots, slot, gslot, n_gslots);
   // workspace rows for values crossing kernels (same interval reuse as generate)
   G.ws_slot.assign(n, -1);
@@ -497,35 +506,57 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     std::ostringstream regions;
     G.calls.clear();
     G.own_f32 = false;
+    const int nph_seg = segs[s].second - segs[s].first;
+    // phase-major layout: every warp reaches the same __syncthreads() (aligned
+    // barrier); a value used by its own warp in a later phase is declared once
+    // at function scope, everything else is local to its phase block
+    std::vector<int> last_own_phase(n, -1);
+    for (int64_t i = 0; i < n; ++i) {
+      if (G.leaf(i) || G.seg_of[i] != s) continue;
+      const Node& x = g.nodes[i];
+      for (int32_t a : {x.a, x.b})
+        if (a >= 0 && !G.leaf(a) && G.seg_of[a] == s && plan.owner[a] == plan.owner[i])
+          last_own_phase[a] = std::max(last_own_phase[a], plan.phase[i]);
+    }
+    std::ostringstream decls;
+    std::vector<std::ostringstream> phase_code(nph_seg);
+    std::vector<std::vector<std::string>> phase_warp(nph_seg, std::vector<std::string>(W));
     for (int w = 0; w < W; ++w) {
       std::ostringstream body;
       std::vector<uint8_t> have(n, 0);
       auto operand = [&](int32_t i, bool want_f64) -> std::string {
         const Node& x = g.nodes[i];
         bool f = G.node_f64(i);
-        std::string name = "v" + std::to_string(i);
         if (x.op == CONST) return lit(x.k, want_f64);
+        // a value this warp loads (input, another warp's value, an earlier
+        // kernel's value) gets its own name; in the phase-major layout it is
+        // declared at function scope because later phases may use it again
+        const bool loaded = x.op == INPUT || G.seg_of[i] != s || plan.owner[i] != w;
+        std::string name = "v" + std::to_string(i) + (aligned && loaded ? "_" + std::to_string(w) : "");
         if (!have[i]) {
+          std::string lhs;
+          if (aligned && loaded) {
+            decls << "  " << G.ty(f) << " " << name << ";\n";
+            lhs = "    " + name;
+          } else {
+            lhs = std::string("    const ") + G.ty(f) + " " + name;
+          }
           if (x.op == INPUT) {
-            body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")"
-                 << (x.bcast ? "Xb[" : "X[") << x.io << "ll * ldx];\n";
+            body << lhs << " = (" << G.ty(f) << ")" << (x.bcast ? "Xb[" : "X[") << x.io << "ll * ldx];\n";
           } else if (G.seg_of[i] != s) {
-            body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")W["
-                 << G.ws_slot[i] << "ll * ldw];\n";
+            body << lhs << " = (" << G.ty(f) << ")W[" << G.ws_slot[i] << "ll * ldw];\n";
           } else if (plan.owner[i] != w) {
             if (slot[i] >= 0)
-              body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")cs_x["
-                   << slot[i] << " * 32 + lane];\n";
+              body << lhs << " = (" << G.ty(f) << ")cs_x[" << slot[i] << " * 32 + lane];\n";
             else
-              body << "    const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")W["
-                   << g_base + gslot[i] << "ll * ldw];\n";
+              body << lhs << " = (" << G.ty(f) << ")W[" << g_base + gslot[i] << "ll * ldw];\n";
           }
           have[i] = 1;
         }
         if (f != want_f64) return std::string("(") + G.ty(want_f64) + ")" + name;
         return name;
       };
-      const int nph = segs[s].second - segs[s].first;
+      const int nph = nph_seg;
       for (int q = 0; q < nph; ++q) {
         for (int64_t i : work[w][q]) {
           const Node& x = g.nodes[i];
@@ -533,7 +564,13 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
           const char* T = G.ty(f);
           std::string A = x.a >= 0 ? operand(x.a, f) : "";
           std::string B = x.b >= 0 ? operand(x.b, f) : "";
-          body << "    const " << T << " v" << i << " = " << op_expr(G, x, f, A, B, o) << ";\n";
+          const bool persists = aligned && plan.phase[i] < last_own_phase[i];
+          if (persists) {
+            decls << "  " << T << " v" << i << ";\n";
+            body << "    v" << i << " = " << op_expr(G, x, f, A, B, o) << ";\n";
+          } else {
+            body << "    const " << T << " v" << i << " = " << op_expr(G, x, f, A, B, o) << ";\n";
+          }
           have[i] = 1;
           if (slot[i] >= 0) body << "    cs_x[" << slot[i] << " * 32 + lane] = (" << tsm << ")v" << i << ";\n";
           if (gslot[i] >= 0) body << "    if (active) W[" << g_base + gslot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
@@ -541,7 +578,13 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
           for (int64_t r : G.out_rows[i])
             body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")v" << i << ";\n";
         }
-        if (q + 1 < nph) body << "    cs_bar();\n";
+        if (aligned) {
+          phase_warp[q][w] = body.str();
+          body.str("");
+          body.clear();
+        } else if (q + 1 < nph) {
+          body << "    cs_bar();\n";
+        }
       }
       if (s == 0 && w == 0) {
         // outputs fed directly by inputs or constants
@@ -551,10 +594,27 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
           for (int64_t r : G.out_rows[i]) body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
         }
       }
+      if (aligned) {
+        if (!body.str().empty()) phase_warp[nph - 1][w] += body.str();
+        continue;
+      }
       regions << (w == 0 ? "  if (warp == 0) {\n" : "  } else if (warp == " + std::to_string(w) + ") {\n")
               << body.str();
     }
-    regions << "  }\n";
+    if (aligned) {
+      regions << decls.str();
+      for (int q = 0; q < nph_seg; ++q) {
+        bool first = true;
+        for (int w = 0; w < W; ++w) {
+          if (phase_warp[q][w].empty()) continue;
+          regions << (first ? "  if (warp == " : "  else if (warp == ") << w << ") {\n" << phase_warp[q][w] << "  }\n";
+          first = false;
+        }
+        if (q + 1 < nph_seg) regions << "  __syncthreads();\n";
+      }
+    } else {
+      regions << "  }\n";
+    }
     std::ostringstream src;
     src << "// Generated cooperative kernel: segment " << s << " of " << nseg << ", " << W
         << " warps per 32 instances, " << (segs[s].second - segs[s].first) << " phases\n";
@@ -574,8 +634,9 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     // without .aligned (bar.sync is the aligned one, defined only when every
     // thread of the CTA executes the same barrier instruction).  Every warp
     // executes the same number of them.
-    src << "static __device__ __forceinline__ void cs_bar() { asm volatile(\"barrier.sync 1, "
-        << 32 * W << ";\" ::: \"memory\"); }\n";
+    if (!aligned)
+      src << "static __device__ __forceinline__ void cs_bar() { asm volatile(\"barrier.sync 1, "
+          << 32 * W << ";\" ::: \"memory\"); }\n";
     std::string name = o.prefix + "_" + std::to_string(s);
     src << "extern \"C\" __global__ void __launch_bounds__(" << 32 * W << ") " << name << "(\n"
         << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin

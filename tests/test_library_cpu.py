@@ -254,21 +254,36 @@ def test_injected_compile_failure_falls_back_to_the_interpreter_under_auto():
 
 @pytest.mark.parametrize("ways", [2, 4, 8, 16])
 def test_cooperative_kernels_reach_every_barrier(ways):
-    """Each warp's region of a cooperative kernel holds the same number of
-    barriers (n_phases - 1), so no warp can wait on a barrier another warp
-    skips; the barrier's thread count equals the CTA size."""
+    """Cooperative kernels are laid out phase by phase: each phase holds one
+    `if (warp == w)` block per warp with work, and the phases are separated by
+    __syncthreads() at function scope, so every thread of the CTA executes the
+    same barrier instructions.  Simulating the phases, every value a warp reads
+    from shared memory or the workspace was written by its owner in an earlier
+    phase and not overwritten before the read."""
     import re as _re
     for ir in (programs.cartpole_rk4(), programs.random_program(3000, seed=ways)):
         fn = L.cusadi_load(ir.to_bytes(), _opt(ways=ways, segment_ops=1200))
         try:
             for seg in range(L.cusadi_info(fn).n_segments):
                 src = L.cusadi_source(fn, False, seg)
-                assert f"barrier.sync 1, {32 * ways};" in src and "bar.sync" not in src.replace("barrier.sync", "")
-                regions = _re.split(r"\n  (?:if|\} else if) \(warp == \d+\) \{\n", src)[1:]
-                assert len(regions) == ways
-                counts = {r.count("cs_bar();") for r in regions}
-                assert len(counts) == 1
-                assert "return" not in "".join(regions)
+                body = src[src.index("if (warp =="):]
+                assert "barrier.sync" not in src and "return" not in body
+                for line in body.splitlines():
+                    if "__syncthreads" in line:
+                        assert line == "  __syncthreads();"
+                phases = body.split("\n  __syncthreads();\n")
+                writes, reads = {}, []
+                for ph, text in enumerate(phases):
+                    for w, block in _re.findall(r"if \(warp == (\d+)\) \{\n(.*?)\n  \}", text, flags=_re.S):
+                        for m in _re.finditer(r"cs_x\[(\d+) \* 32 \+ lane\] = \(\w+\)v(\d+);", block):
+                            writes.setdefault(("s", m.group(1)), []).append((ph, int(w), m.group(2)))
+                        for m in _re.finditer(r"v(\d+)_\d+ = \(\w+\)cs_x\[(\d+) \* 32 \+ lane\];", block):
+                            reads.append((ph, int(w), ("s", m.group(2)), m.group(1)))
+                for ph, w, loc, var in reads:
+                    ws = writes.get(loc, [])
+                    mine = [x for x in ws if x[2] == var]
+                    assert mine and mine[0][0] < ph and mine[0][1] != w
+                    assert not [x for x in ws if x[2] != var and mine[0][0] <= x[0] <= ph]
         finally:
             L.cusadi_free(fn)
 
