@@ -411,9 +411,14 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
 namespace cusadi {
 
 // Cooperative kernels: the CTA's warps split one program; lane l of every warp
-// works on instance 32 * blockIdx.x + l.  Each warp's code is one straight-line
-// region containing exactly n_phases - 1 barriers, so every warp reaches every
-// barrier; values read by another warp are staged in shared memory.
+// works on instance 32 * blockIdx.x + l.  The code is laid out phase by phase:
+// one `if (warp == w)` block per warp with work in that phase, then a
+// __syncthreads() at function scope, so every thread executes the same barrier
+// instructions.  (Per-warp regions with a non-aligned barrier.sync gave wrong
+// results at 6-8 warps with ~160 KB of shared slots on GB300, so that layout
+// is not used.)  Values read by another warp are staged in shared memory
+// (overflow: workspace rows); values a warp needs in a later phase are
+// declared at function scope.
 CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopPlan& plan) {
   CodegenResult R;
   Gen G(g, o);
@@ -461,10 +466,6 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
   int budget_kb = 160;
   if (const char* e = std::getenv("CUSADI_COOP_SHARED_KB")) budget_kb = std::max(0, std::atoi(e));
   const int max_slots = (int)((budget_kb * 1024) / (32 * (sm64 ? 8 : 4)));
-  // CUSADI_COOP_REGIONS=1 selects per-warp regions with a non-aligned barrier
-  // instead of the phase-major layout with __syncthreads()
-  const char* reg_env = std::getenv("CUSADI_COOP_REGIONS");
-  const bool aligned = !(reg_env && reg_env[0] == '1');
   const int n_slots = assign_coop_slots(g, plan, G.seg_of, max_slots, slot, gslot, n_gslots);
   // workspace rows for values crossing kernels (same interval reuse as generate)
   G.ws_slot.assign(n, -1);
@@ -532,10 +533,10 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
         // kernel's value) gets its own name; in the phase-major layout it is
         // declared at function scope because later phases may use it again
         const bool loaded = x.op == INPUT || G.seg_of[i] != s || plan.owner[i] != w;
-        std::string name = "v" + std::to_string(i) + (aligned && loaded ? "_" + std::to_string(w) : "");
+        std::string name = "v" + std::to_string(i) + (loaded ? "_" + std::to_string(w) : "");
         if (!have[i]) {
           std::string lhs;
-          if (aligned && loaded) {
+          if (loaded) {
             decls << "  " << G.ty(f) << " " << name << ";\n";
             lhs = "    " + name;
           } else {
@@ -564,7 +565,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
           const char* T = G.ty(f);
           std::string A = x.a >= 0 ? operand(x.a, f) : "";
           std::string B = x.b >= 0 ? operand(x.b, f) : "";
-          const bool persists = aligned && plan.phase[i] < last_own_phase[i];
+          const bool persists = plan.phase[i] < last_own_phase[i];
           if (persists) {
             decls << "  " << T << " v" << i << ";\n";
             body << "    v" << i << " = " << op_expr(G, x, f, A, B, o) << ";\n";
@@ -578,13 +579,9 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
           for (int64_t r : G.out_rows[i])
             body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")v" << i << ";\n";
         }
-        if (aligned) {
-          phase_warp[q][w] = body.str();
-          body.str("");
-          body.clear();
-        } else if (q + 1 < nph) {
-          body << "    cs_bar();\n";
-        }
+        phase_warp[q][w] = body.str();
+        body.str("");
+        body.clear();
       }
       if (s == 0 && w == 0) {
         // outputs fed directly by inputs or constants
@@ -594,14 +591,9 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
           for (int64_t r : G.out_rows[i]) body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
         }
       }
-      if (aligned) {
-        if (!body.str().empty()) phase_warp[nph - 1][w] += body.str();
-        continue;
-      }
-      regions << (w == 0 ? "  if (warp == 0) {\n" : "  } else if (warp == " + std::to_string(w) + ") {\n")
-              << body.str();
+      if (!body.str().empty()) phase_warp[nph - 1][w] += body.str();
     }
-    if (aligned) {
+    {
       regions << decls.str();
       for (int q = 0; q < nph_seg; ++q) {
         bool first = true;
@@ -612,8 +604,6 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
         }
         if (q + 1 < nph_seg) regions << "  __syncthreads();\n";
       }
-    } else {
-      regions << "  }\n";
     }
     std::ostringstream src;
     src << "// Generated cooperative kernel: segment " << s << " of " << nseg << ", " << W
@@ -629,14 +619,6 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
             << (c.second ? m.d : m.f) << "(a" << (bin ? ", b" : "") << "); }\n";
       }
     }
-    // Barrier 1 over the whole CTA.  The warps reach it from different code
-    // (their own regions), so it must be the non-aligned form: barrier.sync
-    // without .aligned (bar.sync is the aligned one, defined only when every
-    // thread of the CTA executes the same barrier instruction).  Every warp
-    // executes the same number of them.
-    if (!aligned)
-      src << "static __device__ __forceinline__ void cs_bar() { asm volatile(\"barrier.sync 1, "
-          << 32 * W << ";\" ::: \"memory\"); }\n";
     std::string name = o.prefix + "_" + std::to_string(s);
     src << "extern \"C\" __global__ void __launch_bounds__(" << 32 * W << ") " << name << "(\n"
         << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
