@@ -145,7 +145,7 @@ def other_configs(dev, pk64, pk32, flush, reps):
     from oracle import Oracle, tolerance
     from paper_2408_09662_gb300 import inputs, peaks, programs
     from paper_2408_09662_gb300.api import Batch, Function
-    from paper_2408_09662_gb300.rollout import StepProgram, rollout
+    from paper_2408_09662_gb300.rollout import GraphRollout, StepProgram, rollout
 
     out = {}
 
@@ -203,8 +203,18 @@ def other_configs(dev, pk64, pk32, flush, reps):
             L, _ = rollout(prog, x0, K, 50)
             L.backward()
         both = _events_ms(fb, reps, flush)
+        # the same two passes replayed from CUDA graphs (one host launch per pass)
+        gr = GraphRollout(prog, 4096, 50, 10, device=dev)
+        gfwd = _events_ms(lambda: gr.forward(x0.detach(), K.detach()), reps, flush)
+
+        def gfb():
+            gr.forward(x0.detach(), K.detach())
+            gr.backward()
+        gboth = _events_ms(gfb, reps, flush)
         rec[dt] = {"forward_ms": fwd, "backward_ms": both - fwd,
                    "adjoint_forward_ratio": (both - fwd) / fwd,
+                   "graph_forward_ms": gfwd, "graph_backward_ms": gboth - gfwd,
+                   "graph_adjoint_forward_ratio": (gboth - gfwd) / gfwd,
                    "step_ops": int(prog.fn.info.n_ops),
                    "adjoint_ops": int(sum(prog.fn.op_counts(adjoint=True)))}
     out["srb_rollout"] = rec

@@ -82,3 +82,81 @@ def rollout(prog: StepProgram, x0: torch.Tensor, K: torch.Tensor, steps: int,
     """(sum over instances of the running loss after `steps` steps, final states).
     Differentiable with respect to x0 [n, N] and the shared parameters K."""
     return _Rollout.apply(x0, K, prog, steps, checkpoint_every)
+
+
+class GraphRollout:
+    """The same rollout and its gradient replayed from two CUDA graphs (one for
+    the forward pass, one for the checkpointed reverse pass), so the host issues
+    one launch per pass instead of one per step and kernel.  Inputs are copied
+    into static buffers; every call returns (L, x_T, dL/dx0, dL/dK) computed on
+    the device.  The step program's kernels must already be loaded (the
+    constructor runs one eager pass first)."""
+
+    def __init__(self, prog: StepProgram, N: int, steps: int, checkpoint_every: int = 10,
+                 device="cuda"):
+        self.prog, self.steps, self.ce = prog, steps, checkpoint_every
+        dt = prog.fn.torch_dtype
+        P, n = prog.P, prog.n
+        self.x0 = torch.zeros((n, N), dtype=dt, device=device)
+        self.K = torch.zeros(P, dtype=dt, device=device)
+        self.gL = torch.ones((), dtype=dt, device=device)
+        self._eager()                                   # loads forward + adjoint kernels
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream(device)
+        s.wait_stream(torch.cuda.current_stream(device))
+        with torch.cuda.stream(s):
+            self._eager()                               # warm the graph pool
+        torch.cuda.current_stream(device).wait_stream(s)
+        torch.cuda.synchronize()
+        self.g_fwd, self.g_bwd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_fwd):
+            self._forward()
+        with torch.cuda.graph(self.g_bwd):
+            self._backward()
+
+    def _forward(self):
+        prog, P, n = self.prog, self.prog.P, self.prog.n
+        N = self.x0.shape[1]
+        buf = prog.buffers(self.K, N, 2)
+        buf[0, P:P + n] = self.x0
+        self.ckpt = {}
+        for t in range(self.steps):
+            if t % self.ce == 0:
+                self.ckpt[t] = buf[t % 2, P:P + n].clone()
+            prog.step(buf[t % 2], buf[(t + 1) % 2])
+        final = buf[self.steps % 2]
+        self.L = final[P + n].sum()
+        self.xT = final[P:P + n]
+
+    def _backward(self):
+        prog, P, n, steps, ce = self.prog, self.prog.P, self.prog.n, self.steps, self.ce
+        N = self.x0.shape[1]
+        bar = prog.buffers(torch.zeros_like(self.K), N, 2)
+        bar[steps % 2, P + n] = self.gL
+        states = prog.buffers(self.K, N, ce)
+        for start in sorted(self.ckpt, reverse=True):
+            seg = min(ce, steps - start)
+            states[0, P:P + n] = self.ckpt[start]
+            for j in range(seg - 1):
+                prog.step(states[j], states[j + 1])
+            for j in reversed(range(seg)):
+                t = start + j
+                prog.fn.adjoint(states[j], bar[(t + 1) % 2][P:], out=bar[t % 2],
+                                reduce_broadcast=True, accumulate_broadcast=True)
+        self.gx = bar[0, P:P + n]
+        self.gK = bar[0, :P, 0] + bar[1, :P, 0]
+
+    def _eager(self):
+        self._forward()
+        self._backward()
+
+    def forward(self, x0: torch.Tensor, K: torch.Tensor):
+        self.x0.copy_(x0)
+        self.K.copy_(K.reshape(-1))
+        self.g_fwd.replay()
+        return self.L, self.xT
+
+    def backward(self):
+        """dL/dx0, dL/dK of the last forward()."""
+        self.g_bwd.replay()
+        return self.gx, self.gK

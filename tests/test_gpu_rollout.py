@@ -120,3 +120,18 @@ def test_fp32_rollout_gradient_close_to_fp64(prog64):
     L32, _, gx32, gK32 = _grad(prog32, x0, K, 10)
     assert abs(L32 - L64) <= 1e-4 * abs(L64)
     assert np.max(np.abs(gK32 - gK64)) <= 2e-3 * np.max(np.abs(gK64))
+
+
+def test_graph_replayed_rollout_matches_eager(prog64):
+    from paper_2408_09662_gb300.rollout import GraphRollout
+    x0, K = srb_inputs(1024, seed=11)
+    L, xT, gx, gK = _grad(prog64, x0, K, 10)
+    gr = GraphRollout(prog64, 1024, STEPS, 10)
+    for _ in range(2):                       # replay twice with the same inputs
+        Lg, xTg = gr.forward(torch.tensor(x0, device="cuda"), torch.tensor(K.reshape(144), device="cuda"))
+        gxg, gKg = gr.backward()
+        torch.cuda.synchronize()
+        assert float(Lg) == L
+        np.testing.assert_array_equal(xTg.cpu().numpy(), xT)
+        np.testing.assert_array_equal(gxg.cpu().numpy(), gx)
+        np.testing.assert_allclose(gKg.cpu().numpy().reshape(12, 12), gK, rtol=1e-12)
