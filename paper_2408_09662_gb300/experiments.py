@@ -1,22 +1,32 @@
-"""Batch-size sweep of the §IV benchmark family (LDL^T solves of SPD systems,
-each about ten times the operations of the previous one), timed three ways on
-the same inputs: the engine (compiled, or the interpreter beyond the compile
-limit), one launch per atomic op (Fig. 2 right, PyTorch eager) and the CPU
-oracle on all host cores.  Prints a markdown table.
+"""Experiments of the paper reproduced on synthetic inputs; each prints a
+markdown table.
 
-    python -m paper_2408_09662_gb300.experiments ldlt
+    python -m paper_2408_09662_gb300.experiments ldlt   # §IV benchmark family, batch-size sweep
+    python -m paper_2408_09662_gb300.experiments coop   # within-instance parallelism (§VI)
+    python -m paper_2408_09662_gb300.experiments mpc    # MPC cost/violation vs iterations (§V-A, Fig. 4)
+
+ldlt: LDL^T solves of SPD systems, each about ten times the operations of the
+previous one, timed on the same inputs by the engine (compiled, or the
+interpreter beyond the compile limit), by one launch per atomic op (Fig. 2
+right, PyTorch eager), and by a CPU evaluator the caller may pass in.
+coop: the same programs with W warps per 32 instances (``ways``) against one
+thread per instance, at batch sizes too small to fill the GPU.
+mpc: closed-loop simulation of the planar quadrotor under the closed-form MPC
+with M = 1, 2, ... solver iterations (barrier and penalty forms, cold and
+warm-started), reporting time per MPC call, accumulated cost and thrust-bound
+violation -- the axes of Fig. 4.
 """
 from __future__ import annotations
 
-import os
 import statistics
 import sys
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import torch
 
-from . import programs
+from . import inputs, programs
 from .api import Function
 from .vectorized import VectorizedProgram
 
@@ -43,34 +53,167 @@ def _gpu_ms(f, reps=5):
     return statistics.median(ts)
 
 
-def ldlt_sweep(Ns=(1024, 4096, 16384, 65536), vectorized_max_ops=50000):
-    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    from oracle import Oracle
-    cores = os.cpu_count() or 1
-    print("| n | ops | path | N | engine ms | one-launch-per-op ms | CPU oracle ms "
-          f"({cores} cores) | engine vs per-op | engine vs CPU |")
-    print("|---|---|---|---|---|---|---|---|---|")
+def ldlt_sweep(Ns=(1024, 4096, 16384, 65536), vectorized_max_ops=50000, cpu_ms=None):
+    """cpu_ms(ir_bytes, X, n_ops) -> (milliseconds for all N instances, label) or
+    None: an optional CPU baseline supplied by the caller."""
+    label = "CPU ms"
+    rows = []
     for n in programs.LDLT_SIZES:
         ir = programs.ldlt_spd_solve(n)
         irb = ir.to_bytes()
         fn = Function(irb, dtype="f64")
         vec = VectorizedProgram(ir) if ir.count_ops() <= vectorized_max_ops else None
-        orc = Oracle(irb)
         for N in Ns:
             X = _spd(n, N, seed=n)
             x = torch.tensor(X, device="cuda")
             y = fn(x)
             t_eng = _gpu_ms(lambda: fn(x, out=y))
             t_vec = _gpu_ms(lambda: vec(x), reps=2) if vec is not None else float("nan")
-            sample = min(N, max(64, int(2e8 // max(fn.info.n_ops, 1))))
-            t0 = time.perf_counter()
-            orc.eval(X[:, :sample], threads=cores)
-            t_cpu = (time.perf_counter() - t0) * 1e3 * N / sample
-            path = "compiled" if fn.compiled else "interp"
-            print(f"| {n} | {fn.info.n_ops} | {path} | {N} | {t_eng:.4f} | {t_vec:.3f} | {t_cpu:.2f} | "
-                  f"{t_vec / t_eng:.0f}x | {t_cpu / t_eng:.0f}x |", flush=True)
+            t_cpu = float("nan")
+            if cpu_ms is not None:
+                t_cpu, label = cpu_ms(irb, X, fn.info.n_ops)
+            rows.append((n, fn.info.n_ops, "compiled" if fn.compiled else "interp", N,
+                         t_eng, t_vec, t_cpu))
+    print(f"| n | ops | path | N | engine ms | one-launch-per-op ms | {label} | "
+          "engine vs per-op | engine vs CPU |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    for n, ops, path, N, t_eng, t_vec, t_cpu in rows:
+        print(f"| {n} | {ops} | {path} | {N} | {t_eng:.4f} | {t_vec:.3f} | {t_cpu:.2f} | "
+              f"{t_vec / t_eng:.0f}x | {t_cpu / t_eng:.0f}x |", flush=True)
+    return rows
+
+
+def coop_sweep():
+    """Cooperative kernels (W warps per 32 instances) against one thread per
+    instance on batches that leave most of the GPU idle at one thread each."""
+    rng = np.random.default_rng(0)
+    srb_x = np.vstack([np.tile(rng.normal(0, 0.1, (144, 1)), (1, 4096)),
+                       rng.uniform(-0.1, 0.1, (12, 4096)), np.zeros((1, 4096))])
+    mpc_x = np.vstack([rng.uniform(-0.5, 0.5, (6, 4096)), rng.uniform(-1, 1, (2, 4096))])
+    work = [  # (name, program, dtype, N, inputs, ways to try)
+        ("cart-pole RK4 + Jacobian", programs.cartpole_rk4().to_bytes(), "f64", 4096,
+         inputs.cartpole(4096), (0, 2, 4, 8)),
+        ("SRB step", programs.srb_step().to_bytes(), "f64", 4096, srb_x, (0, 4, 8)),
+        ("SRB step", programs.srb_step().to_bytes(), "f32", 4096, srb_x, (0, 4, 8)),
+        ("quadrotor MPC", programs.quadrotor_mpc().to_bytes(), "f64", 4096, mpc_x, (0, 4, 8)),
+        ("random 20k ops", programs.random_program(20000, seed=0).to_bytes(), "f64", 4096,
+         inputs.normal(64, 4096, seed=1), (0, 4, 8)),
+        ("random 200k ops", programs.random_program(200000, seed=107).to_bytes(), "f32", 512,
+         inputs.normal(64, 512, seed=207), (0, 8)),
+    ]
+    cases = [(name, irb, dt, N, X, w) for name, irb, dt, N, X, ws in work for w in ws]
+
+    def build(c):
+        t = time.perf_counter()
+        fn = Function(c[1], dtype=c[2], ways=c[5])
+        return fn, time.perf_counter() - t
+    with ThreadPoolExecutor(6) as ex:
+        fns = list(ex.map(build, cases))
+    print("| program | dtype | N | ways | kernels | ms | speedup vs ways 0 | compile s |")
+    print("|---|---|---|---|---|---|---|---|")
+    base = {}
+    rows = []
+    for (name, _, dt, N, X, w), (fn, ct) in zip(cases, fns):
+        x = torch.tensor(X, dtype=fn.torch_dtype, device="cuda")
+        y = fn(x)
+        ms = _gpu_ms(lambda: fn(x, out=y), reps=9)
+        if w == 0:
+            base[(name, dt, N)] = ms
+        sp = base[(name, dt, N)] / ms
+        rows.append((name, dt, N, w, fn.info.n_segments, ms, sp, ct))
+        print(f"| {name} | {dt} | {N} | {w} | {fn.info.n_segments} | {ms:.4f} | {sp:.2f}x | {ct:.1f} |",
+              flush=True)
+    return rows
+
+
+def _shift_horizon(z, Tn):
+    """Real-time-iteration guess: states and inputs moved one stage earlier,
+    the last stage repeated (in place, rows of z = x_0..x_T, u_0..u_{T-1})."""
+    nx = 6 * (Tn + 1)
+    z[0:6 * Tn] = z[6:nx].clone()
+    z[nx:nx + 2 * (Tn - 1)] = z[nx + 2:nx + 2 * Tn].clone()
+
+
+def mpc_pareto(N=4096, steps=100, Ms=(1, 2, 3, 5, 8), warm_Ms=(1, 2), dtype="f64", seed=0,
+               u_max=8.0, waypoint_range=3.0):
+    """Closed-loop simulation under the closed-form MPC (§V-A): every step
+    solves the MPC for all N quadrotors, applies u_0 and accumulates the stage
+    cost and the thrust-bound violation (quadrotor_closed_loop_step).  Cold
+    start: the program's own guess (hover thrusts, rolled out).  Warm start
+    (real-time iteration, §V-A): the previous solution shifted by one stage.
+    The thrust limit (8, hover is 4.9) and waypoints U(-3, 3)^2 make the bound
+    active early in most runs, so the forms differ in violation."""
+    prm = {"u_max": u_max}
+    p = dict(programs.QUADROTOR, **prm)
+    Tn = p["T"]
+    nz = 6 * (Tn + 1) + 2 * Tn
+    cases = ([(c, M, False) for c in ("barrier", "penalty") for M in Ms] +
+             [(c, M, True) for c in ("barrier", "penalty") for M in warm_Ms])
+
+    def build(c):
+        form, M, warm = c
+        return Function(programs.quadrotor_mpc(dict(prm, M=M), constraint=form,
+                                               warm_start=warm).to_bytes(), dtype=dtype)
+    with ThreadPoolExecutor(6) as ex:
+        fns = list(ex.map(build, cases))
+    cl = Function(programs.quadrotor_closed_loop_step(prm).to_bytes(), dtype=dtype)
+    rng = np.random.default_rng(seed)
+    X0 = np.vstack([rng.uniform(-0.5, 0.5, (6, N)),
+                    rng.uniform(-waypoint_range, waypoint_range, (2, N))])
+    dt = cl.torch_dtype
+    print(f"| form | start | M | ops | kernels | ms per MPC call (N = {N}) | closed-loop cost "
+          "(mean, finite runs) | thrust-bound violation (mean of per-run max) | worst run | diverged |")
+    print("|---|---|---|---|---|---|---|---|---|---|")
+    rows = []
+    for (form, M, warm), fn in zip(cases, fns):
+        buf = torch.zeros((8 + nz + 2, N), dtype=dt, device="cuda")   # x, wp, z, J, V
+        buf[0:8] = torch.tensor(X0, dtype=dt, device="cuda")
+        if warm:                                         # hover guess for the first call
+            buf[8:8 + 6 * (Tn + 1)] = buf[0:6].repeat(Tn + 1, 1)
+            buf[8 + 6 * (Tn + 1):8 + nz] = p["mass"] * p["g"] / 2.0
+        z = torch.empty((nz, N), dtype=dt, device="cuda")
+        nxt = torch.empty((8, N), dtype=dt, device="cuda")
+        ts = []
+        for _ in range(steps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn(buf[0:8 + nz] if warm else buf[0:8], out=z)
+            e.record()
+            buf[8:8 + nz] = z
+            cl(buf, out=nxt)
+            buf[0:6] = nxt[0:6]
+            buf[8 + nz:8 + nz + 2] = nxt[6:8]
+            if warm:
+                _shift_horizon(buf[8:8 + nz], Tn)
+            ts.append((s, e))
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ts)
+        out = buf.double().cpu().numpy()
+        J, V, xs = out[8 + nz], out[8 + nz + 1], out[0:6]
+        ok = np.isfinite(J) & np.all(np.isfinite(xs), axis=0) & np.all(np.abs(xs) < 1e3, axis=0)
+        cost = float(np.mean(J[ok])) if ok.any() else float("nan")
+        Vf = np.where(np.isfinite(V), V, np.inf)
+        viol, worst = float(np.mean(Vf)), float(np.max(Vf))
+        rows.append((form, "warm" if warm else "cold", M, fn.info.n_ops, fn.info.n_segments, ms,
+                     cost, viol, float(1 - ok.mean()), worst))
+        print(f"| {form} | {rows[-1][1]} | {M} | {fn.info.n_ops} | {fn.info.n_segments} | {ms:.3f} | "
+              f"{cost:.5g} | {viol:.3g} | {worst:.3g} | {1 - ok.mean():.3f} |", flush=True)
+    return rows
+
+
+def main(argv):
+    which = argv[1] if len(argv) > 1 else ""
+    if which == "ldlt":
+        ldlt_sweep()
+    elif which == "coop":
+        coop_sweep()
+    elif which == "mpc":
+        mpc_pareto()
+    else:
+        print(__doc__)
+        return 2
+    return 0
 
 
 if __name__ == "__main__":
-    if len(sys.argv) > 1 and sys.argv[1] == "ldlt":
-        ldlt_sweep()
+    sys.exit(main(sys.argv))

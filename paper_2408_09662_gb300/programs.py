@@ -431,6 +431,38 @@ def quadrotor_mpc(params=None, mixed_tags: bool = True, debug_first_step: bool =
     return T.Function(ins, [("z", z)]).to_ir()
 
 
+def quadrotor_closed_loop_step(params=None) -> ProgramIR:
+    """One closed-loop step of the planar quadrotor under the first input of an
+    MPC solution, with the two quantities the paper plots against evaluation
+    time for its MPC (§V-A, Fig. 4): accumulated cost and constraint violation.
+
+    Inputs: x (6), waypoint (2), z (86, an MPC solution laid out as
+    quadrotor_mpc's output: x_0..x_T then u_0..u_{T-1}), J (1), V (1).
+    Outputs: x+ = step(x, u_0) (6), J+ = J + stage cost of (x, u_0) (the MPC's
+    Q, R, x_ref and u_h), V+ = max(V, max_j max(0, u_0j - u_max, -u_0j)).
+    """
+    p = dict(QUADROTOR)
+    if params:
+        p.update(params)
+    Tn = p["T"]
+    g = T.Graph()
+    x, wp, z, J, V = g.symbols(6), g.symbols(2), g.symbols(6 * (Tn + 1) + 2 * Tn), g.symbols(1), g.symbols(1)
+    u = z[6 * (Tn + 1):6 * (Tn + 1) + 2]
+    uh = p["mass"] * p["g"] / 2.0
+    xref = [wp[0], wp[1], 0.0, 0.0, 0.0, 0.0]
+    cost = J[0]
+    for i in range(6):
+        cost = cost + p["q"][i] * (x[i] - xref[i]) * (x[i] - xref[i])
+    for j in range(2):
+        cost = cost + p["r"] * (u[j] - uh) * (u[j] - uh)
+    viol = V[0]
+    for j in range(2):
+        viol = T.fmax(viol, T.fmax(T.fmax(u[j] - p["u_max"], -u[j]), 0.0))
+    xn = quadrotor_step(list(x), list(u), p)
+    return T.Function([("x", x), ("waypoint", wp), ("z", z), ("J", J), ("V", V)],
+                      [("x_next", xn), ("J_next", [cost]), ("V_next", [viol])]).to_ir()
+
+
 # ---------------------------------------------------------------------------
 # Differentiable rollout: single-rigid-body quadruped under linear feedback
 # ---------------------------------------------------------------------------

@@ -103,3 +103,31 @@ def test_mpc_variants_parity(kw):
     idx = np.random.default_rng(6).choice(N, 64, replace=False)
     ref = orc.eval(X[:, idx])
     _check(y[:, idx], ref, tolerance(orc, X[:, idx], ref, 1e-12, kind=0))
+
+
+def test_closed_loop_step_parity():
+    ir = programs.quadrotor_closed_loop_step().to_bytes()
+    N = 4096
+    rng = np.random.default_rng(12)
+    X = np.vstack([rng.uniform(-0.5, 0.5, (6, N)), rng.uniform(-1, 1, (2, N)),
+                   rng.uniform(-1, 16, (86, N)), rng.uniform(0, 5, (2, N))])
+    y = _run(Function(ir, dtype="f64"), X)
+    orc = Oracle(ir)
+    ref = orc.eval(X)
+    _check(y, ref, tolerance(orc, X, ref, 1e-12, kind=0))
+
+
+def test_closed_loop_pareto_small():
+    """The Fig. 4 experiment at a small size: the barrier form keeps every
+    thrust strictly inside its bounds, the penalty form's violation shrinks as
+    its weight grows with M, and more iterations do not raise the cost of a
+    stable closed loop."""
+    from paper_2408_09662_gb300.experiments import mpc_pareto
+    rows = mpc_pareto(N=256, steps=25, Ms=(1, 4), warm_Ms=(1,))
+    by = {(r[0], r[1], r[2]): r for r in rows}
+    for M in (1, 4):
+        assert by[("barrier", "cold", M)][7] == 0.0
+        assert by[("barrier", "cold", M)][8] == 0.0
+    assert by[("penalty", "cold", 4)][7] < 1e-2 * by[("penalty", "cold", 1)][7]
+    assert by[("barrier", "cold", 4)][6] <= by[("barrier", "cold", 1)][6] * 1.05
+    assert all(np.isfinite(r[5]) and r[5] > 0 for r in rows)

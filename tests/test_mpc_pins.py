@@ -155,3 +155,28 @@ def test_warm_start_matches_dense_restatement_and_converges():
         np.testing.assert_allclose(y[:, i], ref, rtol=0, atol=1e-10 * np.max(np.abs(ref)))
     cold = Oracle(programs.quadrotor_mpc({"M": 1, "mu0": 0.001}).to_bytes()).eval(X)
     assert np.max(np.abs(y - z_full)) < 0.01 * np.max(np.abs(cold - z_full))
+
+
+def test_closed_loop_step_matches_model():
+    """The closed-loop step (Fig. 4's cost and constraint-violation axes) against
+    the numpy model's step, a stage cost written out, and the bound violation
+    at hand-picked thrusts (inside, above u_max, below 0)."""
+    ir = programs.quadrotor_closed_loop_step().to_bytes()
+    p = M.QUAD
+    rng = np.random.default_rng(21)
+    N = 6
+    x = rng.uniform(-0.5, 0.5, (6, N))
+    wp = rng.uniform(-1, 1, (2, N))
+    z = rng.uniform(0, 1, (86, N))
+    z[66:68] = np.array([[5.0, 16.5, -0.25, 4.9, 15.0, 0.0], [5.1, 3.0, 7.0, -2.0, 0.0, 14.0]])
+    J, V = rng.uniform(0, 2, (1, N)), np.array([[0.0, 0.0, 0.0, 3.0, 0.0, 0.0]])
+    y = Oracle(ir).eval(np.vstack([x, wp, z, J, V]))
+    uh = p["mass"] * p["g"] / 2
+    want_v = [0.0, 1.5, 0.25, 3.0, 0.0, 0.0]
+    for i in range(N):
+        u = z[66:68, i]
+        xref = np.array([wp[0, i], wp[1, i], 0, 0, 0, 0])
+        cost = J[0, i] + np.sum(np.array(p["q"]) * (x[:, i] - xref) ** 2) + p["r"] * np.sum((u - uh) ** 2)
+        np.testing.assert_allclose(y[:6, i], M.quad_step(x[:, i], u, p), rtol=1e-14, atol=1e-15)
+        assert abs(y[6, i] - cost) <= 1e-13 * cost
+        assert y[7, i] == want_v[i]
