@@ -199,6 +199,34 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
 cusadi_status cusadi_eval_noalloc(cusadi_fn fn, const void* in, int64_t ld_in, void* out,
                                   int64_t ld_out, int64_t N, cusadi_stream stream);
 
+/* y = f(x) from and to host memory: the evaluation with data transfer that
+ * §IV times against the CPU (Fig. 3 reports speedups with and without it).
+ * The instance range is cut into chunks; chunk c's inputs are copied in,
+ * evaluated and copied out on three streams of the library's own (copy-in,
+ * compute, copy-out, ordered by events), so the copies of one chunk overlap
+ * the kernels of its neighbours.
+ *
+ * in_host: [nnz_in x ld_in] and out_host: [nnz_out x ld_out] host buffers of
+ * the dtype's element type, instance-fastest as for cusadi_eval (ld_in >= N,
+ * or >= 1 when every input row is broadcast; ld_out >= N).  Page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister) is needed for the copies to run
+ * asynchronously and overlap; pageable memory gives the same results, slower.
+ * dev_in: [nnz_in x N] and dev_out: [nnz_out x N] device staging buffers with
+ * leading dimension exactly N, owned by the caller; workspace as for
+ * cusadi_eval(N).  chunks: the number of pieces (0 = one per 32,768
+ * instances, between 1 and 8); each piece is a multiple of 32 instances.
+ *
+ * Asynchronous like cusadi_eval: the copies and kernels start after the work
+ * already queued on `stream`, and `stream` waits for all of them, so a
+ * synchronize (or an event) on `stream` makes out_host valid; the host
+ * buffers must stay valid until then.  Calls on one function are enqueued one
+ * at a time (a mutex) and share its three streams.  Errors: INVALID_ARG for
+ * NULL buffers, short leading dimensions, a missing workspace or chunks < 0,
+ * checked before any CUDA call; CUSADI_E_CUDA when a copy or launch fails. */
+cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in, void* out_host,
+                               int64_t ld_out, int64_t N, void* dev_in, void* dev_out,
+                               void* workspace, int32_t chunks, cusadi_stream stream);
+
 /* ---- batched launch of several programs ------------------------------------
  * CusADi puts all operations of a function into one kernel to save launch
  * overhead (§III-A, end).  A batch carries that over to several functions of

@@ -76,6 +76,8 @@ SIGNATURES = {
     "cusadi_adjoint": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                  c_int64, c_uint32, c_void_p, c_void_p]),
     "cusadi_eval_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p]),
+    "cusadi_eval_host": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p,
+                                   c_void_p, c_void_p, c_int32, c_void_p]),
     "cusadi_stream_wait": (c_int32, [c_void_p, c_double]),
     "cusadi_source": (c_int32, [c_void_p, ctypes.c_int, ctypes.c_int, c_char_p, ctypes.POINTER(c_size_t)]),
     "cusadi_batch_create": (c_int32, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t),
@@ -174,6 +176,12 @@ def cusadi_adjoint(fn: int, inp: int, ld_in: int, out_bar: int, ld_ob: int, in_b
 def cusadi_eval_noalloc(fn: int, inp: int, ld_in: int, out: int, ld_out: int, N: int,
                         stream: int) -> None:
     check(lib().cusadi_eval_noalloc(fn, inp, ld_in, out, ld_out, N, stream), "cusadi_eval_noalloc")
+
+
+def cusadi_eval_host(fn: int, in_host: int, ld_in: int, out_host: int, ld_out: int, N: int,
+                     dev_in: int, dev_out: int, workspace: int, chunks: int, stream: int) -> None:
+    check(lib().cusadi_eval_host(fn, in_host, ld_in, out_host, ld_out, N, dev_in, dev_out,
+                                 workspace, chunks, stream), "cusadi_eval_host")
 
 
 def cusadi_stream_wait(stream: int, timeout_seconds: float) -> None:

@@ -61,6 +61,7 @@ class Function:
         self.inputs = [L.cusadi_arg_info(self._fn, False, j) for j in range(self.info.n_in)]
         self.outputs = [L.cusadi_arg_info(self._fn, True, j) for j in range(self.info.n_out)]
         self._ws = {}
+        self._stage = {}
 
     def __del__(self):
         if getattr(self, "_fn", None):
@@ -116,6 +117,43 @@ class Function:
         L.cusadi_eval(self._fn, x.data_ptr(), self._ld(x), out.data_ptr(), self._ld(out), N,
                       ws.data_ptr() if ws is not None else 0,
                       torch.cuda.current_stream(x.device).cuda_stream)
+        return out
+
+    def eval_host(self, x: torch.Tensor, out: torch.Tensor | None = None, chunks: int = 0,
+                  sync: bool = True, device=None) -> torch.Tensor:
+        """y = f(x) for host tensors: x [nnz_in, N] on the CPU (pinned for the
+        copies to overlap the kernels), y returned (or filled) on the CPU.  The
+        library copies chunks in, evaluates and copies them out on its own
+        streams; device staging buffers are kept between calls.  With
+        sync=False the result is valid once the current stream reaches this
+        point (an event or a synchronize)."""
+        if x.is_cuda:
+            raise ValueError("x must be a host tensor (use __call__ for device tensors)")
+        if x.dtype != self.torch_dtype:
+            raise TypeError(f"x must be {self.torch_dtype}, got {x.dtype}")
+        if x.dim() != 2 or x.shape[0] != self.nnz_in or x.stride(1) != 1:
+            raise ValueError(f"x must be [{self.nnz_in}, N] with unit stride along N")
+        N = x.shape[1]
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if out is None:
+            out = torch.empty((self.nnz_out, N), dtype=self.torch_dtype, pin_memory=x.is_pinned())
+        if out.is_cuda or out.dtype != self.torch_dtype or out.dim() != 2 or \
+                out.shape != (self.nnz_out, N) or out.stride(1) != 1:
+            raise ValueError(f"out must be a host tensor [{self.nnz_out}, N] of {self.torch_dtype}")
+        key = (N, str(dev))
+        st = self._stage.get(key)
+        if st is None:
+            st = (torch.empty((self.nnz_in, N), dtype=self.torch_dtype, device=dev),
+                  torch.empty((self.nnz_out, N), dtype=self.torch_dtype, device=dev))
+            self._stage = {key: st}                 # keep one staging pair
+        ws = self.workspace(N, False, dev)
+        stream = torch.cuda.current_stream(dev)
+        with torch.cuda.device(dev):
+            L.cusadi_eval_host(self._fn, x.data_ptr(), self._ld(x), out.data_ptr(), self._ld(out), N,
+                               st[0].data_ptr(), st[1].data_ptr(),
+                               ws.data_ptr() if ws is not None else 0, chunks, stream.cuda_stream)
+        if sync:
+            stream.synchronize()
         return out
 
     def adjoint(self, x: torch.Tensor, ybar: torch.Tensor, out: torch.Tensor | None = None,

@@ -154,6 +154,11 @@ struct DevState {
   double* d_k_fwd = nullptr;
   void* d_ops_adj = nullptr;
   double* d_k_adj = nullptr;
+  // host-buffer evaluation: a copy-in and a copy-out stream, one compute
+  // stream per chunk, and the events that order them (created on first use)
+  cudaStream_t h_in = nullptr, h_out = nullptr;
+  std::vector<cudaStream_t> h_comp;
+  std::vector<cudaEvent_t> hev;
 };
 
 // One compiled or packed evaluation direction (forward or adjoint).
@@ -183,6 +188,7 @@ struct cusadi_fn_s {
   std::string compile_fallback;   // why AUTO fell back to the interpreter, if it did
   std::mutex dev_mu;
   std::map<int, DevState> dev;
+  std::mutex host_mu;             // serialises the enqueue of host-buffer evaluations
 };
 
 namespace {
@@ -553,6 +559,10 @@ void cusadi_free(cusadi_fn fn) {
       if (ds.d_k_fwd) cudaFree(ds.d_k_fwd);
       if (ds.d_ops_adj) cudaFree(ds.d_ops_adj);
       if (ds.d_k_adj) cudaFree(ds.d_k_adj);
+      if (ds.h_in) cudaStreamDestroy(ds.h_in);
+      if (ds.h_out) cudaStreamDestroy(ds.h_out);
+      for (cudaStream_t st : ds.h_comp) cudaStreamDestroy(st);
+      for (cudaEvent_t e : ds.hev) cudaEventDestroy(e);
     }
   }
   delete fn;
@@ -642,6 +652,110 @@ cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out
   cusadi_status s = device_state(fn, false, &ds);
   if (s != CUSADI_OK) return s;
   return run(fn, fn->fwd, *ds, false, in, ld_in, nullptr, 0, out, ld_out, N, workspace, 0, 0, stream);
+}
+
+static int32_t host_chunks(int64_t N) {
+  // at least 8,192 instances a chunk: the copies of a chunk are then long
+  // enough to run at full bandwidth, and neighbouring chunks' kernels overlap
+  return (int32_t)std::max<int64_t>(1, std::min<int64_t>(8, N / 8192));
+}
+
+cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in, void* out_host,
+                               int64_t ld_out, int64_t N, void* dev_in, void* dev_out,
+                               void* workspace, int32_t chunks, cusadi_stream stream) {
+  if (!fn) return fail(CUSADI_E_INVALID_ARG, "fn is NULL");
+  if (N < 0) return fail(CUSADI_E_INVALID_ARG, "N must be >= 0");
+  if (chunks < 0) return fail(CUSADI_E_INVALID_ARG, "chunks must be >= 0");
+  if (N == 0 || fn->ir.nnz_out == 0) return CUSADI_OK;
+  if (N > ((int64_t)1 << 40)) return fail(CUSADI_E_INVALID_ARG, "N too large");
+  const int64_t nin = fn->ir.nnz_in, nout = fn->ir.nnz_out;
+  const Graph& g = fn->fwd.g;
+  if (nin > 0) {
+    if (!in_host) return fail(CUSADI_E_INVALID_ARG, "in_host is NULL");
+    if (!dev_in) return fail(CUSADI_E_INVALID_ARG, "dev_in is NULL");
+    int64_t need = all_bcast(g, nin) ? 1 : N;
+    if (ld_in < need) return fail(CUSADI_E_INVALID_ARG, "ld_in smaller than N");
+  }
+  if (!out_host) return fail(CUSADI_E_INVALID_ARG, "out_host is NULL");
+  if (!dev_out) return fail(CUSADI_E_INVALID_ARG, "dev_out is NULL");
+  if (ld_out < N) return fail(CUSADI_E_INVALID_ARG, "ld_out smaller than N");
+  if (direction_ws(fn, fn->fwd, N) > 0 && !workspace)
+    return fail(CUSADI_E_INVALID_ARG, "this function needs a workspace (cusadi_workspace_bytes)");
+  DevState* ds;
+  cusadi_status st = device_state(fn, false, &ds);
+  if (st != CUSADI_OK) return st;
+
+  const int64_t C = std::min<int64_t>(chunks > 0 ? chunks : host_chunks(N), (N + 31) / 32);
+  const int64_t chunk = round_up((N + C - 1) / C, 32);
+  const int64_t n_chunks = (N + chunk - 1) / chunk;
+  const size_t elt = elt_io(fn->opt.dtype);
+  // without a workspace every chunk's kernels get a stream of their own, so a
+  // chunk starts as soon as its inputs are in and its CTAs fill the SMs that
+  // the previous chunks' tails leave free; a workspace is shared by every
+  // chunk, so then the kernels stay on one stream
+  const bool own = direction_ws(fn, fn->fwd, N) == 0;
+  std::lock_guard<std::mutex> lk(fn->host_mu);
+  cudaError_t ce;
+  for (cudaStream_t* h : {&ds->h_in, &ds->h_out})
+    if (!*h && (ce = cudaStreamCreateWithFlags(h, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail("cudaStreamCreateWithFlags", ce);
+  while (ds->h_comp.size() < (size_t)(own ? n_chunks : 1)) {
+    cudaStream_t h;
+    if ((ce = cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail("cudaStreamCreateWithFlags", ce);
+    ds->h_comp.push_back(h);
+  }
+  const size_t n_ev = 2 * (size_t)n_chunks + 2;
+  while (ds->hev.size() < n_ev) {
+    cudaEvent_t e;
+    if ((ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail("cudaEventCreateWithFlags", ce);
+    ds->hev.push_back(e);
+  }
+  cudaStream_t s_in = ds->h_in, s_out = ds->h_out;
+  cudaEvent_t ev_start = ds->hev[0], ev_end = ds->hev[1];
+  // everything already queued on the caller's stream happens first
+  if ((ce = cudaEventRecord(ev_start, (cudaStream_t)stream)) != cudaSuccess) return cuda_fail("cudaEventRecord", ce);
+  std::vector<cudaStream_t> all = {s_in, s_out};
+  all.insert(all.end(), ds->h_comp.begin(), ds->h_comp.begin() + (own ? n_chunks : 1));
+  for (cudaStream_t h : all)
+    if ((ce = cudaStreamWaitEvent(h, ev_start, 0)) != cudaSuccess) return cuda_fail("cudaStreamWaitEvent", ce);
+  const char* hin = (const char*)in_host;
+  char* din = (char*)dev_in;
+  for (int64_t c = 0; c < n_chunks; ++c) {
+    const int64_t s0 = c * chunk, n = std::min(chunk, N - s0);
+    cudaEvent_t ev_in = ds->hev[2 + 2 * c], ev_comp = ds->hev[3 + 2 * c];
+    // inputs: runs of consecutive rows; a broadcast row's value goes to the
+    // chunk's first column, where the kernel (given the chunk's base) reads it
+    for (int64_t r0 = 0; r0 < nin;) {
+      const bool bc = r0 < (int64_t)g.in_bcast.size() && g.in_bcast[r0];
+      int64_t r1 = r0 + 1;
+      while (r1 < nin && (r1 < (int64_t)g.in_bcast.size() && g.in_bcast[r1]) == bc) ++r1;
+      ce = cudaMemcpy2DAsync(din + ((size_t)r0 * N + s0) * elt, (size_t)N * elt,
+                             hin + ((size_t)r0 * ld_in + (bc ? 0 : s0)) * elt, (size_t)ld_in * elt,
+                             (bc ? 1 : (size_t)n) * elt, (size_t)(r1 - r0), cudaMemcpyHostToDevice, s_in);
+      if (ce != cudaSuccess) return cuda_fail("cudaMemcpy2DAsync (inputs)", ce);
+      r0 = r1;
+    }
+    cudaStream_t s_comp = ds->h_comp[own ? c : 0];
+    if ((ce = cudaEventRecord(ev_in, s_in)) != cudaSuccess) return cuda_fail("cudaEventRecord", ce);
+    if ((ce = cudaStreamWaitEvent(s_comp, ev_in, 0)) != cudaSuccess) return cuda_fail("cudaStreamWaitEvent", ce);
+    st = run(fn, fn->fwd, *ds, false, din + (size_t)s0 * elt, N, nullptr, 0,
+             (char*)dev_out + (size_t)s0 * elt, N, n, workspace, 0, 0, (cusadi_stream)s_comp);
+    if (st != CUSADI_OK) return st;
+    if ((ce = cudaEventRecord(ev_comp, s_comp)) != cudaSuccess) return cuda_fail("cudaEventRecord", ce);
+    if ((ce = cudaStreamWaitEvent(s_out, ev_comp, 0)) != cudaSuccess) return cuda_fail("cudaStreamWaitEvent", ce);
+    ce = cudaMemcpy2DAsync((char*)out_host + (size_t)s0 * elt, (size_t)ld_out * elt,
+                           (const char*)dev_out + (size_t)s0 * elt, (size_t)N * elt, (size_t)n * elt,
+                           (size_t)nout, cudaMemcpyDeviceToHost, s_out);
+    if (ce != cudaSuccess) return cuda_fail("cudaMemcpy2DAsync (outputs)", ce);
+  }
+  // the copy-out stream has waited for every chunk's kernels, and each of
+  // those for its copy-in, so its last event covers the whole evaluation
+  if ((ce = cudaEventRecord(ev_end, s_out)) != cudaSuccess) return cuda_fail("cudaEventRecord", ce);
+  if ((ce = cudaStreamWaitEvent((cudaStream_t)stream, ev_end, 0)) != cudaSuccess)
+    return cuda_fail("cudaStreamWaitEvent", ce);
+  return CUSADI_OK;
 }
 
 cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,

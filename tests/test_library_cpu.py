@@ -144,6 +144,26 @@ def test_eval_argument_errors_are_caught_on_the_host():
         L.cusadi_free(fn)
 
 
+def test_eval_host_argument_errors_are_caught_on_the_host():
+    fn = L.cusadi_load(programs.listing2().to_bytes(), _opt())
+    try:
+        L.cusadi_eval_host(fn, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)             # N = 0 is a no-op
+        bad = [(fn, 8, 16, 8, 16, -1, 8, 8, 0, 0, 0),                    # N < 0
+               (fn, 0, 16, 8, 16, 16, 8, 8, 0, 0, 0),                    # NULL host input
+               (fn, 8, 16, 8, 16, 16, 0, 8, 0, 0, 0),                    # NULL device input
+               (fn, 8, 16, 0, 16, 16, 8, 8, 0, 0, 0),                    # NULL host output
+               (fn, 8, 16, 8, 16, 16, 8, 0, 0, 0, 0),                    # NULL device output
+               (fn, 8, 8, 8, 16, 16, 8, 8, 0, 0, 0),                     # ld_in < N
+               (fn, 8, 16, 8, 8, 16, 8, 8, 0, 0, 0),                     # ld_out < N
+               (fn, 8, 16, 8, 16, 16, 8, 8, 0, -1, 0)]                   # chunks < 0
+        for args in bad:
+            with pytest.raises(L.CusadiError) as e:
+                L.cusadi_eval_host(*args)
+            assert e.value.status == L.CUSADI_E_INVALID_ARG, args
+    finally:
+        L.cusadi_free(fn)
+
+
 def test_segmented_program_needs_a_workspace():
     ir = programs.random_program(3000, n_in=16, n_out=8, seed=5).to_bytes()
     fn = L.cusadi_load(ir, _opt(segment_ops=700, dtype=L.CUSADI_F32))
