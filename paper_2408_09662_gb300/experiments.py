@@ -4,6 +4,7 @@ markdown table.
     python -m paper_2408_09662_gb300.experiments ldlt   # §IV benchmark family, batch-size sweep
     python -m paper_2408_09662_gb300.experiments coop   # within-instance parallelism (§VI)
     python -m paper_2408_09662_gb300.experiments mpc    # MPC cost/violation vs iterations (§V-A, Fig. 4)
+    python -m paper_2408_09662_gb300.experiments one random20k f64 4096 8   # one kernel, for a profiler
 
 ldlt: LDL^T solves of SPD systems, each about ten times the operations of the
 previous one, timed on the same inputs by the engine (compiled, or the
@@ -201,6 +202,21 @@ def mpc_pareto(N=4096, steps=100, Ms=(1, 2, 3, 5, 8), warm_Ms=(1, 2), dtype="f64
     return rows
 
 
+def one_kernel(program="random20k", dtype="f64", N=4096, ways=0, reps=3):
+    """Compile one program and launch it `reps` times (a small case for a profiler)."""
+    irs = {"random20k": lambda: programs.random_program(20000, seed=0),
+           "cartpole": programs.cartpole_rk4, "mpc": programs.quadrotor_mpc,
+           "lqr": programs.quadrotor_lqr_step, "srb": programs.srb_step}
+    fn = Function(irs[program]().to_bytes(), dtype=dtype, ways=ways)
+    x = torch.tensor(inputs.normal(fn.nnz_in, N, seed=1), dtype=fn.torch_dtype, device="cuda")
+    y = fn(x)
+    for _ in range(reps):
+        fn(x, out=y)
+    torch.cuda.synchronize()
+    print(f"{program} {dtype} N={N} ways={ways}: {fn.info.n_segments} kernel(s), "
+          f"{_gpu_ms(lambda: fn(x, out=y)):.4f} ms")
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else ""
     if which == "ldlt":
@@ -209,6 +225,10 @@ def main(argv):
         coop_sweep()
     elif which == "mpc":
         mpc_pareto()
+    elif which == "one":
+        # one <program> <dtype> <N> <ways>
+        prog, dt, N, w = (argv[2:] + ["random20k", "f64", "4096", "0"][len(argv) - 2:])[:4]
+        one_kernel(prog, dt, int(N), int(w))
     else:
         print(__doc__)
         return 2
