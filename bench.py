@@ -117,9 +117,15 @@ def cpu_oracle_baseline(ir: bytes, x: np.ndarray, sample: int):
     t = time.perf_counter()
     y = orc.eval(xs, threads=cores)
     dt = time.perf_counter() - t
+    s1 = min(sample, 4096)                  # one core, on a smaller sample
+    t = time.perf_counter()
+    orc.eval(xs[:, :s1], threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": sample / dt, "unit": "instance-evals/s", "cores": cores, "kind": "oracle",
             "sample": f"{sample} of the {N_INST} instances, FP64 interpreter, {cores} threads, "
-                      f"{dt:.2f} s wall"}, y
+                      f"{dt:.2f} s wall",
+            "single_core": {"value": s1 / dt1, "unit": "instance-evals/s",
+                            "sample": f"{s1} instances, 1 thread, {dt1:.2f} s wall"}}, y
 
 
 def _events_ms(fn, reps, flush):
@@ -250,6 +256,21 @@ def other_configs(dev, pk64, pk32, flush, reps):
                    "graph_adjoint_forward_ratio": (gboth - gfwd) / gfwd,
                    "step_ops": int(prog.fn.info.n_ops),
                    "adjoint_ops": int(sum(prog.fn.op_counts(adjoint=True)))}
+        # the step's forward and adjoint kernels alone at N = 65,536 (roofline points)
+        fn, Nk = prog.fn, 65536
+        rk = np.random.default_rng(1)
+        Xk = np.vstack([np.tile(Kn.reshape(144, 1), (1, Nk)), rk.uniform(-0.1, 0.1, (12, Nk)),
+                        np.zeros((1, Nk))])
+        xk = torch.tensor(Xk, dtype=tdt, device=dev)
+        yk = fn(xk)
+        ybar = torch.ones_like(yk)
+        xbar = fn.adjoint(xk, ybar, reduce_broadcast=True)
+        ms_f = _events_ms(lambda: fn(xk, out=yk), reps, flush)
+        ms_a = _events_ms(lambda: fn.adjoint(xk, ybar, out=xbar, reduce_broadcast=True), reps, flush)
+        rec[dt]["kernels_N65536"] = {
+            "forward_ms": ms_f, "adjoint_ms": ms_a, "adjoint_forward_ratio": ms_a / ms_f,
+            "forward_roofline_frac": peaks.roofline_seconds(fn, pk64, pk32) * Nk / (ms_f * 1e-3),
+            "adjoint_roofline_frac": peaks.roofline_seconds(fn, pk64, pk32, adjoint=True) * Nk / (ms_a * 1e-3)}
     out["srb_rollout"] = rec
 
     # --- f1 LQR closed-loop step (SDA Riccati solve inside), N = 10,000, FP64 ---

@@ -227,6 +227,21 @@ cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in,
                                int64_t ld_out, int64_t N, void* dev_in, void* dev_out,
                                void* workspace, int32_t chunks, cusadi_stream stream);
 
+/* Output argument `arg` as a dense matrix per instance.  The engine reads and
+ * writes only structural non-zeros (§II-A: sparse CasADi matrices, Listing 2
+ * stores nnz entries); this scatters one argument of an evaluation result for
+ * a caller that wants the full nrow x ncol block (a PyTorch tensor, §III-B).
+ * y: [nnz_out x ld_y] as cusadi_eval wrote it; dense: [nrow*ncol x ld_d],
+ * entry (r, c) of instance i at dense[(r*ncol + c)*ld_d + i], structural zeros
+ * written as 0; both device buffers of the dtype's element type, owned by the
+ * caller; ld_y, ld_d >= N.  The first call for an argument on a device
+ * uploads an nrow*ncol index map (it allocates and synchronises: make it
+ * before any stream capture); later calls launch one kernel on `stream`.
+ * Errors: INVALID_ARG for a bad index, NULL buffers or short leading
+ * dimensions, checked before any CUDA call. */
+cusadi_status cusadi_densify(cusadi_fn fn, int arg, const void* y, int64_t ld_y, void* dense,
+                             int64_t ld_d, int64_t N, cusadi_stream stream);
+
 /* ---- batched launch of several programs ------------------------------------
  * CusADi puts all operations of a function into one kernel to save launch
  * overhead (§III-A, end).  A batch carries that over to several functions of

@@ -76,6 +76,8 @@ SIGNATURES = {
     "cusadi_adjoint": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                  c_int64, c_uint32, c_void_p, c_void_p]),
     "cusadi_eval_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p]),
+    "cusadi_densify": (c_int32, [c_void_p, ctypes.c_int, c_void_p, c_int64, c_void_p, c_int64, c_int64,
+                                 c_void_p]),
     "cusadi_eval_host": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p,
                                    c_void_p, c_void_p, c_int32, c_void_p]),
     "cusadi_stream_wait": (c_int32, [c_void_p, c_double]),
@@ -182,6 +184,11 @@ def cusadi_eval_host(fn: int, in_host: int, ld_in: int, out_host: int, ld_out: i
                      dev_in: int, dev_out: int, workspace: int, chunks: int, stream: int) -> None:
     check(lib().cusadi_eval_host(fn, in_host, ld_in, out_host, ld_out, N, dev_in, dev_out,
                                  workspace, chunks, stream), "cusadi_eval_host")
+
+
+def cusadi_densify(fn: int, arg: int, y: int, ld_y: int, dense: int, ld_d: int, N: int,
+                   stream: int) -> None:
+    check(lib().cusadi_densify(fn, arg, y, ld_y, dense, ld_d, N, stream), "cusadi_densify")
 
 
 def cusadi_stream_wait(stream: int, timeout_seconds: float) -> None:

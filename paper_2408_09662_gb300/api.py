@@ -119,6 +119,17 @@ class Function:
                       torch.cuda.current_stream(x.device).cuda_stream)
         return out
 
+    def dense(self, y: torch.Tensor, arg: int) -> torch.Tensor:
+        """Output argument `arg` of a result y [nnz_out, N] as a dense
+        [nrow, ncol, N] tensor (structural zeros filled in on the GPU)."""
+        self._check(y, self.nnz_out, "y")
+        a = self.outputs[arg]
+        N = y.shape[1]
+        d = torch.empty((a.nrow, a.ncol, N), dtype=self.torch_dtype, device=y.device)
+        L.cusadi_densify(self._fn, arg, y.data_ptr(), self._ld(y), d.data_ptr(), max(N, 1), N,
+                         torch.cuda.current_stream(y.device).cuda_stream)
+        return d
+
     def eval_host(self, x: torch.Tensor, out: torch.Tensor | None = None, chunks: int = 0,
                   sync: bool = True, device=None) -> torch.Tensor:
         """y = f(x) for host tensors: x [nnz_in, N] on the CPU (pinned for the

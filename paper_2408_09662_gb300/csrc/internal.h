@@ -154,6 +154,9 @@ int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, con
                   void* stream);
 // threads per block of the shared-memory interpreter (0: work vector too long)
 int interp_block(int64_t n_slots, int dtype);
+// dense copy of one output argument (kernels.cu); returns a cudaError_t value
+int launch_densify(int dtype, const void* y, int64_t ldy, int64_t off, const int32_t* map,
+                   int64_t n_dense, void* dense, int64_t ldd, int64_t N, int sms, void* stream);
 
 // runtime.cpp: NVRTC compile with the in-memory and on-disk content-hash cache
 bool compile_nvrtc(const std::string& src, const std::string& name,

@@ -6,6 +6,7 @@
 // fits, else in a global workspace in the instance-fastest layout.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <type_traits>
@@ -160,6 +161,39 @@ int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, con
                 : launch<float, float, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st);
   return smem ? launch<float, double, true, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st)
               : launch<float, double, true, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st);
+}
+
+// Dense copy of one sparse output argument: dense[k * ldd + i] = y[(off +
+// map[k]) * ldy + i] where map[k] >= 0 (a structural non-zero), else 0.  k
+// runs over the nrow * ncol entries (row-major); the grid covers (k, i) with
+// instances fastest so loads and stores are coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) densify_kernel(const T* __restrict__ y, int64_t ldy,
+                                                      int64_t off, const int32_t* __restrict__ map,
+                                                      int64_t n_dense, T* __restrict__ dense,
+                                                      int64_t ldd, int64_t N) {
+  const int64_t total = n_dense * N;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / N, i = t - k * N;
+    const int32_t src = map[k];
+    dense[k * ldd + i] = src >= 0 ? y[(off + src) * ldy + i] : T(0);
+  }
+}
+
+int launch_densify(int dtype, const void* y, int64_t ldy, int64_t off, const int32_t* map,
+                   int64_t n_dense, void* dense, int64_t ldd, int64_t N, int sms, void* stream) {
+  const int64_t total = n_dense * N;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)std::max(sms, 1) * 8);
+  if (blocks <= 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == CUSADI_F64)
+    densify_kernel<double><<<(unsigned)blocks, 256, 0, st>>>((const double*)y, ldy, off, map, n_dense,
+                                                           (double*)dense, ldd, N);
+  else
+    densify_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((const float*)y, ldy, off, map, n_dense,
+                                                          (float*)dense, ldd, N);
+  return (int)cudaGetLastError();
 }
 
 }  // namespace cusadi

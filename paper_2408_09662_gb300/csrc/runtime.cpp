@@ -158,6 +158,7 @@ struct DevState {
   // stream per chunk, and the events that order them (created on first use)
   cudaStream_t h_in = nullptr, h_out = nullptr;
   std::vector<cudaStream_t> h_comp;
+  std::map<int, int32_t*> dense_map;  // output argument -> dense index map (device)
   std::vector<cudaEvent_t> hev;
 };
 
@@ -562,6 +563,7 @@ void cusadi_free(cusadi_fn fn) {
       if (ds.h_in) cudaStreamDestroy(ds.h_in);
       if (ds.h_out) cudaStreamDestroy(ds.h_out);
       for (cudaStream_t st : ds.h_comp) cudaStreamDestroy(st);
+      for (auto& m : ds.dense_map) cudaFree(m.second);
       for (cudaEvent_t e : ds.hev) cudaEventDestroy(e);
     }
   }
@@ -652,6 +654,43 @@ cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out
   cusadi_status s = device_state(fn, false, &ds);
   if (s != CUSADI_OK) return s;
   return run(fn, fn->fwd, *ds, false, in, ld_in, nullptr, 0, out, ld_out, N, workspace, 0, 0, stream);
+}
+
+cusadi_status cusadi_densify(cusadi_fn fn, int arg, const void* y, int64_t ld_y, void* dense,
+                             int64_t ld_d, int64_t N, cusadi_stream stream) {
+  if (!fn) return fail(CUSADI_E_INVALID_ARG, "fn is NULL");
+  if (arg < 0 || arg >= (int)fn->ir.out.size()) return fail(CUSADI_E_INVALID_ARG, "output index out of range");
+  if (N < 0) return fail(CUSADI_E_INVALID_ARG, "N must be >= 0");
+  const Arg& a = fn->ir.out[arg];
+  const int64_t n_dense = (int64_t)a.nrow * a.ncol;
+  if (N == 0 || n_dense == 0) return CUSADI_OK;
+  if (!y || !dense) return fail(CUSADI_E_INVALID_ARG, "NULL buffer");
+  if (ld_y < N || ld_d < N) return fail(CUSADI_E_INVALID_ARG, "leading dimension smaller than N");
+  DevState* ds;
+  cusadi_status st = device_state(fn, false, &ds);
+  if (st != CUSADI_OK) return st;
+  int32_t* map = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(fn->dev_mu);
+    auto it = ds->dense_map.find(arg);
+    if (it != ds->dense_map.end()) {
+      map = it->second;
+    } else {
+      std::vector<int32_t> h(n_dense, -1);
+      for (int64_t r = 0; r < a.nrow; ++r)
+        for (int64_t p = a.rowptr[r]; p < a.rowptr[r + 1]; ++p) h[r * a.ncol + a.col[p]] = (int32_t)p;
+      cudaError_t ce = cudaMalloc((void**)&map, h.size() * sizeof(int32_t));
+      if (ce != cudaSuccess) return cuda_fail("cudaMalloc", ce);
+      if ((ce = cudaMemcpy(map, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(map);
+        return cuda_fail("cudaMemcpy", ce);
+      }
+      ds->dense_map[arg] = map;
+    }
+  }
+  int rc = launch_densify(fn->opt.dtype, y, ld_y, a.offset, map, n_dense, dense, ld_d, N, ds->sms, stream);
+  if (rc != 0) return fail(CUSADI_E_CUDA, std::string("densify launch: ") + cudaGetErrorString((cudaError_t)rc));
+  return CUSADI_OK;
 }
 
 static int32_t host_chunks(int64_t N) {

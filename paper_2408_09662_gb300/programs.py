@@ -237,6 +237,23 @@ def quadrotor_step_jacobian(x, u, p):
     return J
 
 
+def quadrotor_step_sparse_jacobian(params=None) -> ProgramIR:
+    """x+ = step(x, u) of the planar quadrotor and its 6 x 8 Jacobian d x+ /
+    d [x; u] by the tracer's forward mode, stored sparse: entries whose tangent
+    is structurally zero are not in the output's CSR pattern (§II-A)."""
+    p = dict(QUADROTOR)
+    if params:
+        p.update(params)
+    g = T.Graph()
+    x, u = g.symbols(6), g.symbols(2)
+    xn = quadrotor_step(list(x), list(u), p)
+    J = T.jacobian(xn, list(x) + list(u))
+    mask = [[not (isinstance(v, float) and v == 0.0) for v in row] for row in J]
+    vals = [v for row, mrow in zip(J, mask) for v, m in zip(row, mrow) if m]
+    return T.Function([("x", x), ("u", u)],
+                      [("x_next", xn), ("jac", vals, Sparsity.from_mask(mask))]).to_ir()
+
+
 def kkt_order(Tn: int):
     """Stage ordering of the KKT unknowns: x0, lam0, then per stage k:
     u_k, x_{k+1}, lam_{k+1}.  Entries are (kind, stage, component).

@@ -269,3 +269,35 @@ def test_stream_wait_times_out_then_completes():
         L.cusadi_stream_wait(s, 0.001)
     assert e.value.status == L.CUSADI_E_TIMEOUT
     L.cusadi_stream_wait(s, 60.0)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_densified_sparse_output_matches_oracle(dtype):
+    """cusadi_densify: the structural non-zeros of the quadrotor step's sparse
+    Jacobian land at their (row, col) and every other entry is exactly 0."""
+    ir = programs.quadrotor_step_sparse_jacobian()
+    fn = Function(ir.to_bytes(), dtype=dtype)
+    N = 10007
+    rng = np.random.default_rng(32)
+    X = np.vstack([rng.uniform(-1, 1, (6, N)), rng.uniform(0, 10, (2, N))])
+    if dtype == "f32":
+        X = X.astype(np.float32).astype(np.float64)
+    x = torch.tensor(X, dtype=fn.torch_dtype, device="cuda")
+    y = fn(x)
+    D = fn.dense(y, 1)
+    Dx = fn.dense(y, 0)
+    torch.cuda.synchronize()
+    D, Dx, y = D.double().cpu().numpy(), Dx.double().cpu().numpy(), y.double().cpu().numpy()
+    sp = ir.outputs[1]
+    mask = np.zeros((6, 8), bool)
+    for r in range(6):
+        for q in range(sp.rowptr[r], sp.rowptr[r + 1]):
+            assert np.array_equal(D[r, sp.col[q]], y[6 + q])    # a copy, bit for bit
+            mask[r, sp.col[q]] = True
+    assert np.all(D[~mask] == 0.0)
+    np.testing.assert_array_equal(Dx[:, 0], y[:6])
+    orc = Oracle(ir.to_bytes())
+    idx = np.random.default_rng(33).choice(N, 64, replace=False)
+    ref = orc.eval(X[:, idx])
+    tol = tolerance(orc, X[:, idx], ref, 1e-12 if dtype == "f64" else 2e-4, kind=0 if dtype == "f64" else 1)
+    assert np.all(np.abs(y[:, idx] - ref) <= tol)
