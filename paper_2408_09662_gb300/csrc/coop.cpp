@@ -2,14 +2,21 @@
 // instances (lane = instance), splitting one program's ops between them.
 //
 // CusADi parallelises across instances only and names parallelism inside one
-// expression graph as future work (§VI).  Here a list scheduler assigns every
-// op to a warp (earliest finish time, with a fixed cost for a value that has
-// to cross to another warp), then ops are grouped into phases: an op runs in
-// the phase of its latest same-warp operand, or one phase after an operand
-// produced by another warp.  Phases are separated by a CTA barrier and values
-// that cross warps go through shared memory.
+// expression graph as future work (§VI).  Ops are assigned a warp and a phase;
+// phases are separated by a CTA barrier, an op may read a value of its own
+// warp from its own or an earlier phase and a value of another warp from an
+// earlier phase (through shared memory).  Two schedulers are tried and the
+// one with the lower estimated time (sum over phases of the busiest warp's
+// op cost plus a barrier cost) is kept:
+//  * earliest finish time: each op goes to the warp where it finishes first,
+//    counting a fixed cost for a value that crosses warps; phases follow;
+//  * phase packing: phases are filled one at a time, up to a target cost per
+//    warp, always with the ready op of longest remaining critical path (bottom
+//    level), so every warp carries about the same work between barriers.
+//    Several targets are tried.
 #include <algorithm>
 #include <map>
+#include <queue>
 
 #include "internal.h"
 
@@ -29,9 +36,124 @@ double op_cost(int op) {
   }
 }
 
+constexpr double kBarrierCost = 6.0;   // a CTA barrier plus the shared-memory hand-off, in op costs
+
+bool is_leaf(const Graph& g, int64_t i) { return g.nodes[i].op == INPUT || g.nodes[i].op == CONST; }
+
+// sum over phases of (the busiest warp's op cost + one barrier)
+double estimate(const Graph& g, const CoopPlan& P) {
+  std::vector<double> load((size_t)P.n_phases * P.ways, 0.0);
+  for (int64_t i = 0; i < (int64_t)g.nodes.size(); ++i)
+    if (!is_leaf(g, i)) load[(size_t)P.phase[i] * P.ways + P.owner[i]] += op_cost(g.nodes[i].op);
+  double t = 0;
+  for (int q = 0; q < P.n_phases; ++q)
+    t += *std::max_element(load.begin() + (size_t)q * P.ways, load.begin() + (size_t)(q + 1) * P.ways) +
+         kBarrierCost;
+  return t;
+}
+
+struct Ready {
+  double pri;
+  int64_t i;
+  bool operator<(const Ready& o) const { return pri < o.pri || (pri == o.pri && i > o.i); }
+};
+
+CoopPlan plan_packed(const Graph& g, int ways, double target, const std::vector<double>& bottom,
+                     const std::vector<std::vector<int64_t>>& users) {
+  const int64_t n = (int64_t)g.nodes.size();
+  CoopPlan P;
+  P.ways = ways;
+  P.owner.assign(n, -1);
+  P.phase.assign(n, 0);
+  std::vector<int> pending(n, 0);
+  int64_t todo = 0;
+  std::priority_queue<Ready> open;                        // any warp may take these
+  std::vector<std::priority_queue<Ready>> mine(ways);     // need a value of this warp's phase
+  std::vector<int64_t> later;                             // need values of two warps' phase
+  for (int64_t i = 0; i < n; ++i) {
+    if (is_leaf(g, i)) continue;
+    ++todo;
+    for (int32_t o : {g.nodes[i].a, g.nodes[i].b})
+      if (o >= 0 && !is_leaf(g, o)) ++pending[i];
+    if (pending[i] == 0) open.push({bottom[i], i});
+  }
+  int q = 0;
+  std::vector<double> load(ways);
+  std::vector<char> full(ways);
+  while (todo > 0) {
+    std::fill(load.begin(), load.end(), 0.0);
+    std::fill(full.begin(), full.end(), 0);
+    int active = ways;
+    while (active > 0) {
+      int w = -1;
+      for (int k = 0; k < ways; ++k)
+        if (!full[k] && (w < 0 || load[k] < load[w])) w = k;
+      const bool has_mine = !mine[w].empty(), has_open = !open.empty();
+      if (!has_mine && !has_open) { full[w] = 1; --active; continue; }
+      const bool take_mine = has_mine && (!has_open || !(mine[w].top() < open.top()));
+      const Ready r = take_mine ? mine[w].top() : open.top();
+      const double c = op_cost(g.nodes[r.i].op);
+      if (load[w] > 0 && load[w] + c > target) { full[w] = 1; --active; continue; }
+      (take_mine ? mine[w] : open).pop();
+      P.owner[r.i] = w;
+      P.phase[r.i] = q;
+      load[w] += c;
+      --todo;
+      for (int64_t u : users[r.i]) {
+        if (--pending[u] != 0) continue;
+        int same = -1;   // warp of the operands computed in this phase, -2 if two warps
+        for (int32_t o : {g.nodes[u].a, g.nodes[u].b})
+          if (o >= 0 && !is_leaf(g, o) && P.phase[o] == q)
+            same = (same == -1 || same == P.owner[o]) ? P.owner[o] : -2;
+        if (same == -1) open.push({bottom[u], u});
+        else if (same >= 0) mine[same].push({bottom[u], u});
+        else later.push_back(u);
+      }
+    }
+    // what waited on this phase's values of one warp, or of two, is open next phase
+    for (auto& m : mine)
+      while (!m.empty()) { open.push(m.top()); m.pop(); }
+    for (int64_t u : later) open.push({bottom[u], u});
+    later.clear();
+    ++q;
+  }
+  P.n_phases = std::max(q, 1);
+  return P;
+}
+
+CoopPlan plan_eft(const Graph& g, int ways, double comm_cost);
+
 }  // namespace
 
 CoopPlan plan_coop(const Graph& g, int ways, double comm_cost) {
+  const int64_t n = (int64_t)g.nodes.size();
+  // bottom level: op cost on the longest path from the op to the end
+  std::vector<double> bottom(n, 0.0);
+  std::vector<std::vector<int64_t>> users(n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (is_leaf(g, i)) continue;
+    bottom[i] = op_cost(g.nodes[i].op);
+    for (int32_t o : {g.nodes[i].a, g.nodes[i].b})
+      if (o >= 0 && !is_leaf(g, o)) users[o].push_back(i);
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    if (is_leaf(g, i)) continue;
+    for (int32_t o : {g.nodes[i].a, g.nodes[i].b})
+      if (o >= 0 && !is_leaf(g, o)) bottom[o] = std::max(bottom[o], op_cost(g.nodes[o].op) + bottom[i]);
+  }
+  CoopPlan best = plan_eft(g, ways, comm_cost);
+  double best_t = estimate(g, best);
+  for (double target : {8.0, 16.0, 32.0, 64.0, 128.0, 256.0, 512.0}) {
+    CoopPlan P = plan_packed(g, ways, target, bottom, users);
+    const double t = estimate(g, P);
+    if (t < best_t) { best_t = t; best = std::move(P); }
+  }
+  return best;
+}
+
+namespace {
+
+CoopPlan plan_eft(const Graph& g, int ways, double comm_cost) {
   const int64_t n = (int64_t)g.nodes.size();
   CoopPlan P;
   P.ways = ways;
@@ -69,6 +191,8 @@ CoopPlan plan_coop(const Graph& g, int ways, double comm_cost) {
     if (!leaf(i)) P.n_phases = std::max(P.n_phases, P.phase[i] + 1);
   return P;
 }
+
+}  // namespace
 
 int assign_coop_slots(const Graph& g, const CoopPlan& P, const std::vector<int>& seg_of_node,
                       int max_slots, std::vector<int>& slot, std::vector<int>& gslot,
