@@ -157,7 +157,9 @@ size_t cusadi_workspace_bytes(cusadi_fn fn, int64_t N, int adjoint);
  * buffer whose rows are all broadcast may use ld_in >= 1).  workspace: at least
  * cusadi_workspace_bytes(fn, N, 0) bytes, or NULL when that is 0.  N = 0 is a
  * no-op.  The first call on a device loads the device module (not capturable
- * in a CUDA graph); later calls only launch kernels on `stream`. */
+ * in a CUDA graph); later calls only launch kernels on `stream`.  Calls that
+ * may overlap on the GPU (different streams) need workspaces of their own:
+ * the kernels write the workspace. */
 cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out,
                           int64_t ld_out, int64_t N, void* workspace, cusadi_stream stream);
 
@@ -202,9 +204,9 @@ cusadi_status cusadi_eval_noalloc(cusadi_fn fn, const void* in, int64_t ld_in, v
 /* y = f(x) from and to host memory: the evaluation with data transfer that
  * §IV times against the CPU (Fig. 3 reports speedups with and without it).
  * The instance range is cut into chunks; chunk c's inputs are copied in,
- * evaluated and copied out on three streams of the library's own (copy-in,
- * compute, copy-out, ordered by events), so the copies of one chunk overlap
- * the kernels of its neighbours.
+ * evaluated and copied out on streams of the library's own (one copy-in, one
+ * copy-out and one compute stream per chunk, ordered by events), so the
+ * copies of one chunk overlap the kernels of the others.
  *
  * in_host: [nnz_in x ld_in] and out_host: [nnz_out x ld_out] host buffers of
  * the dtype's element type, instance-fastest as for cusadi_eval (ld_in >= N,
@@ -213,14 +215,15 @@ cusadi_status cusadi_eval_noalloc(cusadi_fn fn, const void* in, int64_t ld_in, v
  * asynchronously and overlap; pageable memory gives the same results, slower.
  * dev_in: [nnz_in x N] and dev_out: [nnz_out x N] device staging buffers with
  * leading dimension exactly N, owned by the caller; workspace as for
- * cusadi_eval(N).  chunks: the number of pieces (0 = one per 32,768
- * instances, between 1 and 8); each piece is a multiple of 32 instances.
+ * cusadi_eval(N) (each chunk uses its own columns of it).  chunks: the number
+ * of pieces (0 = two from N = 16,384 on, else one); each piece is a multiple
+ * of 32 instances (128 on the interpreter path).
  *
  * Asynchronous like cusadi_eval: the copies and kernels start after the work
  * already queued on `stream`, and `stream` waits for all of them, so a
  * synchronize (or an event) on `stream` makes out_host valid; the host
  * buffers must stay valid until then.  Calls on one function are enqueued one
- * at a time (a mutex) and share its three streams.  Errors: INVALID_ARG for
+ * at a time (a mutex) and share its streams.  Errors: INVALID_ARG for
  * NULL buffers, short leading dimensions, a missing workspace or chunks < 0,
  * checked before any CUDA call; CUSADI_E_CUDA when a copy or launch fails. */
 cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in, void* out_host,
@@ -274,7 +277,9 @@ size_t cusadi_batch_workspace_bytes(cusadi_batch b);
  * mode: CUSADI_BATCH_PERSISTENT or CUSADI_BATCH_PLAIN.  The first call on a
  * device loads the module, uploads the tile table and captures the graph
  * (allocates; not capturable); later calls only copy the buffer table when
- * it changed (a few hundred bytes) and launch. */
+ * it changed (a few hundred bytes) and launch.  The buffer table and the tile
+ * counter belong to the batch (one per device), so calls on one batch must not
+ * overlap on the GPU: issue them on one stream, or order them with events. */
 cusadi_status cusadi_batch_eval(cusadi_batch b, const void* const* in, const int64_t* ld_in,
                                 void* const* out, const int64_t* ld_out, void* workspace,
                                 int mode, cusadi_stream stream);

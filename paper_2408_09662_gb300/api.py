@@ -60,7 +60,6 @@ class Function:
         self.torch_dtype = torch.float64 if dtype == "f64" else torch.float32
         self.inputs = [L.cusadi_arg_info(self._fn, False, j) for j in range(self.info.n_in)]
         self.outputs = [L.cusadi_arg_info(self._fn, True, j) for j in range(self.info.n_out)]
-        self._ws = {}
         self._stage = {}
 
     def __del__(self):
@@ -83,15 +82,14 @@ class Function:
         return L.cusadi_source(self._fn, adjoint, segment)
 
     def workspace(self, N: int, adjoint: bool = False, device=None) -> torch.Tensor | None:
+        """A fresh workspace for one call.  PyTorch's caching allocator ties the
+        block to the current stream, so calls on different streams never share
+        one (a single cached buffer would race between concurrent calls), and
+        on the same stream the block is reused in stream order at no cost."""
         nb = L.cusadi_workspace_bytes(self._fn, N, adjoint)
         if nb == 0:
             return None
-        key = (adjoint, str(device))
-        ws = self._ws.get(key)
-        if ws is None or ws.numel() < nb:
-            ws = torch.empty(nb, dtype=torch.uint8, device=device)
-            self._ws[key] = ws
-        return ws
+        return torch.empty(nb, dtype=torch.uint8, device=device)
 
     @staticmethod
     def _ld(t: torch.Tensor) -> int:
@@ -252,6 +250,8 @@ class Batch:
         self.block = block
 
     def workspace(self, device) -> torch.Tensor | None:
+        """One workspace kept for the batch: calls on one batch must not overlap
+        on the GPU anyway (its buffer table and tile counter are shared)."""
         nb = L.cusadi_batch_workspace_bytes(self._b)
         if nb == 0:
             return None

@@ -381,14 +381,16 @@ bool all_bcast(const Graph& g, int64_t rows) {
   return true;
 }
 
+// ldw > 0: the workspace's leading dimension when W points into a larger
+// workspace (a chunk of a bigger batch); otherwise the one for N instances.
 cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const void* X,
                   int64_t ldx, const void* X2, int64_t ldx2, void* Y, int64_t ldy, int64_t N,
-                  void* W, int acc, int reduce, cusadi_stream stream) {
+                  void* W, int acc, int reduce, cusadi_stream stream, int64_t ldw = 0) {
   if (fn->path == CUSADI_PATH_INTERP) {
     int rc = launch_interp((const IOp*)(adjoint ? ds.d_ops_adj : ds.d_ops_fwd),
                            (int64_t)d.ip.ops.size(), adjoint ? ds.d_k_adj : ds.d_k_fwd,
                            fn->opt.dtype, X, ldx, X2 ? X2 : X, ldx2, adjoint ? fn->ir.nnz_in : (int64_t)1 << 40,
-                           Y, ldy, N, W, interp_ldw(N), d.ip.n_slots, acc, reduce, stream);
+                           Y, ldy, N, W, ldw > 0 ? ldw : interp_ldw(N), d.ip.n_slots, acc, reduce, stream);
     if (rc != 0) return fail(CUSADI_E_CUDA, std::string("interpreter launch: ") + cudaGetErrorString((cudaError_t)rc));
     return CUSADI_OK;
   }
@@ -405,7 +407,7 @@ cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const 
     grid = (unsigned)((N + 31) / 32);
     smem = (unsigned)d.cg.smem_bytes;
   }
-  long long lx = ldx, lx2 = ldx2, ly = ldy, n = N, lw = round_up(N, 32);
+  long long lx = ldx, lx2 = ldx2, ly = ldy, n = N, lw = ldw > 0 ? ldw : round_up(N, 32);
   const void* x2 = X2 ? X2 : X;
   for (size_t s = 0; s < fs.size(); ++s) {
     void* args[] = {(void*)&X, &lx, (void*)&x2, &lx2, &Y, &ly, &n, &W, &lw, &acc, &reduce};
@@ -694,9 +696,10 @@ cusadi_status cusadi_densify(cusadi_fn fn, int arg, const void* y, int64_t ld_y,
 }
 
 static int32_t host_chunks(int64_t N) {
-  // at least 8,192 instances a chunk: the copies of a chunk are then long
-  // enough to run at full bandwidth, and neighbouring chunks' kernels overlap
-  return (int32_t)std::max<int64_t>(1, std::min<int64_t>(8, N / 8192));
+  // two chunks from 16,384 instances: half the copy time hides behind the
+  // other chunk's kernels, and each chunk still fills the GPU (more, smaller
+  // concurrent launches were measured to slow some programs down)
+  return N >= 16384 ? 2 : 1;
 }
 
 cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in, void* out_host,
@@ -724,21 +727,22 @@ cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in,
   cusadi_status st = device_state(fn, false, &ds);
   if (st != CUSADI_OK) return st;
 
-  const int64_t C = std::min<int64_t>(chunks > 0 ? chunks : host_chunks(N), (N + 31) / 32);
-  const int64_t chunk = round_up((N + C - 1) / C, 32);
+  // every chunk's kernels get a stream of their own, so a chunk starts as soon
+  // as its inputs are in and its CTAs fill the SMs that the previous chunks'
+  // tails leave free.  Each chunk uses its own columns of the workspace (the
+  // interpreter writes whole 128-thread blocks of columns, hence its grain).
+  const int64_t grain = fn->path == CUSADI_PATH_INTERP ? 128 : 32;
+  const int64_t C = std::min<int64_t>(chunks > 0 ? chunks : host_chunks(N), (N + grain - 1) / grain);
+  const int64_t chunk = round_up((N + C - 1) / C, grain);
   const int64_t n_chunks = (N + chunk - 1) / chunk;
   const size_t elt = elt_io(fn->opt.dtype);
-  // without a workspace every chunk's kernels get a stream of their own, so a
-  // chunk starts as soon as its inputs are in and its CTAs fill the SMs that
-  // the previous chunks' tails leave free; a workspace is shared by every
-  // chunk, so then the kernels stay on one stream
-  const bool own = direction_ws(fn, fn->fwd, N) == 0;
+  const int64_t ldw = fn->path == CUSADI_PATH_INTERP ? interp_ldw(N) : round_up(N, 32);
   std::lock_guard<std::mutex> lk(fn->host_mu);
   cudaError_t ce;
   for (cudaStream_t* h : {&ds->h_in, &ds->h_out})
     if (!*h && (ce = cudaStreamCreateWithFlags(h, cudaStreamNonBlocking)) != cudaSuccess)
       return cuda_fail("cudaStreamCreateWithFlags", ce);
-  while (ds->h_comp.size() < (size_t)(own ? n_chunks : 1)) {
+  while (ds->h_comp.size() < (size_t)n_chunks) {
     cudaStream_t h;
     if ((ce = cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking)) != cudaSuccess)
       return cuda_fail("cudaStreamCreateWithFlags", ce);
@@ -756,7 +760,7 @@ cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in,
   // everything already queued on the caller's stream happens first
   if ((ce = cudaEventRecord(ev_start, (cudaStream_t)stream)) != cudaSuccess) return cuda_fail("cudaEventRecord", ce);
   std::vector<cudaStream_t> all = {s_in, s_out};
-  all.insert(all.end(), ds->h_comp.begin(), ds->h_comp.begin() + (own ? n_chunks : 1));
+  all.insert(all.end(), ds->h_comp.begin(), ds->h_comp.begin() + n_chunks);
   for (cudaStream_t h : all)
     if ((ce = cudaStreamWaitEvent(h, ev_start, 0)) != cudaSuccess) return cuda_fail("cudaStreamWaitEvent", ce);
   const char* hin = (const char*)in_host;
@@ -776,11 +780,12 @@ cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in,
       if (ce != cudaSuccess) return cuda_fail("cudaMemcpy2DAsync (inputs)", ce);
       r0 = r1;
     }
-    cudaStream_t s_comp = ds->h_comp[own ? c : 0];
+    cudaStream_t s_comp = ds->h_comp[c];
     if ((ce = cudaEventRecord(ev_in, s_in)) != cudaSuccess) return cuda_fail("cudaEventRecord", ce);
     if ((ce = cudaStreamWaitEvent(s_comp, ev_in, 0)) != cudaSuccess) return cuda_fail("cudaStreamWaitEvent", ce);
+    void* wc = workspace ? (void*)((char*)workspace + (size_t)s0 * elt_ws(fn->opt.dtype)) : nullptr;
     st = run(fn, fn->fwd, *ds, false, din + (size_t)s0 * elt, N, nullptr, 0,
-             (char*)dev_out + (size_t)s0 * elt, N, n, workspace, 0, 0, (cusadi_stream)s_comp);
+             (char*)dev_out + (size_t)s0 * elt, N, n, wc, 0, 0, (cusadi_stream)s_comp, ldw);
     if (st != CUSADI_OK) return st;
     if ((ce = cudaEventRecord(ev_comp, s_comp)) != cudaSuccess) return cuda_fail("cudaEventRecord", ce);
     if ((ce = cudaStreamWaitEvent(s_out, ev_comp, 0)) != cudaSuccess) return cuda_fail("cudaStreamWaitEvent", ce);

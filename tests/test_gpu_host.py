@@ -77,3 +77,30 @@ def test_asynchronous_call_orders_with_the_stream():
     ev.record()
     ev.synchronize()
     np.testing.assert_array_equal(out.numpy(), _device(fn, X))
+
+
+@pytest.mark.parametrize("chunks", [2, 5])
+def test_segmented_mpc_chunks_run_concurrently(chunks):
+    """The MPC program passes values between its two kernels through the
+    workspace; concurrent chunks use disjoint columns of it."""
+    fn = Function(programs.quadrotor_mpc().to_bytes(), dtype="f64")
+    assert fn.info.n_segments >= 2
+    N = 20000
+    rng = np.random.default_rng(41)
+    X = np.vstack([rng.uniform(-0.5, 0.5, (6, N)), rng.uniform(-1, 1, (2, N))])
+    y = fn.eval_host(torch.tensor(X).pin_memory(), chunks=chunks)
+    np.testing.assert_array_equal(y.numpy(), _device(fn, X))
+
+
+def test_interpreter_with_global_workspace_chunks():
+    """A work vector too long for shared memory: the interpreter keeps it in the
+    workspace, 128-column grain per chunk."""
+    ir = programs.ldlt_spd_solve(47).to_bytes()        # 1,176 live slots
+    fn = Function(ir, dtype="f64", path="interp")
+    assert fn.workspace(1000) is not None
+    N = 3000
+    rng = np.random.default_rng(10)
+    X = rng.uniform(-1, 1, (fn.nnz_in, N))
+    X[[k * (k + 3) // 2 for k in range(47)]] += 60.0      # diagonal entries: diagonally dominant
+    y = fn.eval_host(torch.tensor(X).pin_memory(), chunks=3)
+    np.testing.assert_array_equal(y.numpy(), _device(fn, X))
