@@ -165,7 +165,9 @@ def other_configs(dev, pk64, pk32, flush, reps):
     def make_batch():
         t0 = time.perf_counter()
         irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(sizes)]
-        return Batch(irs, [N for _, N in sizes], dtype="f32"), time.perf_counter() - t0
+        # ways=4: programs with few instances and many ops (here the 50k-200k-op
+        # ones) run as cooperative tiles in the 128-thread scheduler
+        return Batch(irs, [N for _, N in sizes], dtype="f32", ways=4), time.perf_counter() - t0
     ir3 = programs.quadrotor_mpc().to_bytes()
     ir1 = programs.quadrotor_lqr_step().to_bytes()
     srb = programs.srb_step().to_bytes()
@@ -301,14 +303,23 @@ def other_configs(dev, pk64, pk32, flush, reps):
     xs = [torch.tensor(inputs.normal(64, N, seed=200 + j), dtype=torch.float32, device=dev)
           for j, (_, N) in enumerate(sizes)]
     outs = [torch.empty((32, N), dtype=torch.float32, device=dev) for _, N in sizes]
-    block = b.tune(xs, outs, reps=3)
+    by_block = {}
+    for blk in (32, 64, 128):            # 128: with cooperative tiles
+        b.set_block(blk)
+        b(xs, outs, mode="persistent")
+        by_block[blk] = _events_ms(lambda: b(xs, outs, mode="persistent"), reps, flush)
+    block = min(by_block, key=by_block.get)
+    b.set_block(block)
     ms_p = _events_ms(lambda: b(xs, outs, mode="persistent"), reps, flush)
     ms_s = _events_ms(lambda: b(xs, outs, mode="plain"), reps, flush)
     gen_ops = sum(n * N for n, N in sizes)
     out["uneven_batch_f32"] = {
         "programs": [{"ops_generated": n, "N": N} for n, N in sizes],
         "op_instances_generated": gen_ops, "persistent_ms": ms_p, "plain_8_launches_ms": ms_s,
-        "speedup_persistent_vs_plain": ms_s / ms_p, "tile_block": block, **b.info(),
+        "speedup_persistent_vs_plain": ms_s / ms_p, "tile_block": block,
+        "persistent_ms_by_tile_block": {str(k): v for k, v in by_block.items()},
+        "cooperative_tiles": "ways=4 in the 128-thread scheduler for programs with N <= 8192 "
+                             "and >= 10,000 ops", **b.info(),
         "gop_per_s_generated": gen_ops / (ms_p * 1e-3) * 1e-9, "setup_seconds": t_compile}
     return out
 

@@ -263,8 +263,13 @@ cusadi_status cusadi_densify(cusadi_fn fn, int arg, const void* y, int64_t ld_y,
 /* Compiles and links n programs (irs[j] of nbytes[j] bytes) for N[j]
  * instances each.  opt: dtype, block (32, 64 or 128: instances per tile),
  * maxrregcount, fmad, schedule, segment_ops, compile_threads, cache_dir;
- * path and compile_limit_ops are ignored (always compiled).  n <= 32.
- * Errors: INVALID_ARG, INVALID_IR, COMPILE, OOM. */
+ * path and compile_limit_ops are ignored (always compiled).  ways: 0, or 4 to
+ * give programs with N[j] <= 8192 and >= 10,000 ops cooperative tiles: the
+ * 128-thread scheduler then runs such a program 32 instances per tile with
+ * its 4 warps splitting the program between them (parallelism inside one
+ * expression graph, which CusADi leaves to future work, §VI), so a long
+ * program with few instances stops setting the length of the launch.
+ * n <= 32.  Errors: INVALID_ARG, INVALID_IR, COMPILE, OOM. */
 cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, const int64_t* N,
                                   int n, const cusadi_options* opt, cusadi_batch* out);
 void cusadi_batch_free(cusadi_batch b);

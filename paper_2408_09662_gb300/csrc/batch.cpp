@@ -51,10 +51,22 @@ struct BatchProg {
   Graph g;
   CodegenResult cg;
   std::vector<std::string> bins;
+  CodegenResult ccg;             // cooperative device functions (4 warps per 32 instances)
+  std::vector<std::string> cbins;
+  bool coop = false;
   int64_t N = 0, n_ops = 0;
   size_t ws_off = 0;
   int64_t ldw = 0;
 };
+
+// Cooperative tiles: in the 128-thread scheduler, a program with few
+// instances and many ops is run 32 instances per tile by the CTA's 4 warps
+// together (within-instance parallelism), so its tiles stop being the longest
+// chains of the launch.
+constexpr int kCoopWays = 4;
+constexpr int kCoopVariant = 2;                  // the 128-thread scheduler
+constexpr int64_t kCoopMaxN = 8192, kCoopMinOps = 10000;
+constexpr int kCoopSharedKB = 96;
 
 struct BatchDev {
   bool ready = false;
@@ -63,6 +75,7 @@ struct BatchDev {
   std::vector<CUfunction> plain;
   int grid[kVariants] = {};
   void* d_tiles[kVariants] = {};
+  unsigned smem = 0;                         // dynamic shared memory of the 128-thread scheduler
   unsigned* d_ticket = nullptr;
   BArg* d_args = nullptr;
   std::vector<BArg> last;
@@ -82,6 +95,7 @@ struct cusadi_batch_s {
   std::vector<BTile> tiles[kVariants];
   int variant = 2;
   size_t ws_bytes = 0;
+  int64_t coop_smem = 0;         // largest shared-memory need of a cooperative program
   int registers = 0;
   std::mutex mu;
   std::map<int, BatchDev> dev;
@@ -105,6 +119,24 @@ std::string scheduler_source(const cusadi_batch_s& b) {
       s << "extern \"C\" __device__ void " << seg.name << "(const " << T << "* __restrict__, long long, const "
         << T << "* __restrict__, long long, " << T << "* __restrict__, long long, " << TW
         << "* __restrict__, long long, long long);\n";
+  for (size_t p = 0; p < b.progs.size(); ++p)
+    for (auto& seg : b.progs[p].ccg.segs)
+      s << "extern \"C\" __device__ void " << seg.name << "(const " << T << "* __restrict__, long long, "
+        << T << "* __restrict__, long long, " << TW << "* __restrict__, long long, long long, int, "
+        << "unsigned char* __restrict__);\n";
+  s << "static __device__ __forceinline__ void cs_run_coop(const BArg* __restrict__ A, int p, "
+    << "long long first, int count, unsigned char* smem) {\n  switch (p) {\n";
+  for (size_t p = 0; p < b.progs.size(); ++p) {
+    if (!b.progs[p].coop) continue;
+    s << "    case " << p << ": {\n      const BArg a = A[" << p << "];\n";
+    for (auto& seg : b.progs[p].ccg.segs)
+      s << "      " << seg.name << "(a.X, a.ldx, a.Y, a.ldy, a.W, a.ldw, first, count, smem);\n";
+    s << "      break;\n    }\n";
+  }
+  s << "  }\n}\n";
+  s << "__device__ __constant__ unsigned char cs_coop[" << std::max<size_t>(b.progs.size(), 1) << "] = {";
+  for (size_t p = 0; p < b.progs.size(); ++p) s << (p ? ", " : "") << (b.progs[p].coop ? 1 : 0);
+  s << "};\n";
   s << "static __device__ __forceinline__ void cs_run(const BArg* __restrict__ A, int p, long long i) {\n"
     << "  switch (p) {\n";
   for (size_t p = 0; p < b.progs.size(); ++p) {
@@ -116,19 +148,25 @@ std::string scheduler_source(const cusadi_batch_s& b) {
   s << "  }\n}\n";
   for (int v = 0; v < kVariants; ++v) {
     const int B = kBlocks[v];
+    const bool coop = v == kCoopVariant;
     s << "extern \"C\" __global__ void __launch_bounds__(" << B << ") cs_batch_" << B
       << "(const BTile* __restrict__ tiles, int n_tiles, unsigned int* ticket,\n"
       << "    const BArg* __restrict__ A) {\n"
-      << "  __shared__ int s_t;\n"
-      << "  for (;;) {\n"
+      << "  __shared__ int s_t;\n";
+    if (coop) s << "  extern __shared__ __align__(16) unsigned char cs_dyn[];\n";
+    s << "  for (;;) {\n"
       << "    if (threadIdx.x == 0) s_t = (int)atomicAdd(ticket, 1u);\n"
       << "    __syncthreads();\n"
       << "    const int t = s_t;\n"
       << "    __syncthreads();\n"
       << "    if (t >= n_tiles) return;\n"
-      << "    const BTile tl = tiles[t];\n"
-      << "    if ((int)threadIdx.x < tl.count) cs_run(A, tl.prog, tl.first + threadIdx.x);\n"
-      << "  }\n}\n";
+      << "    const BTile tl = tiles[t];\n";
+    if (coop)   // the tile is the same for the whole CTA, so every thread takes the same branch
+      s << "    if (cs_coop[tl.prog]) cs_run_coop(A, tl.prog, tl.first, tl.count, cs_dyn);\n"
+        << "    else if ((int)threadIdx.x < tl.count) cs_run(A, tl.prog, tl.first + threadIdx.x);\n";
+    else
+      s << "    if ((int)threadIdx.x < tl.count) cs_run(A, tl.prog, tl.first + threadIdx.x);\n";
+    s << "  }\n}\n";
   }
   for (size_t p = 0; p < b.progs.size(); ++p)
     s << "extern \"C\" __global__ void __launch_bounds__(128) cs_plain_" << p
@@ -183,12 +221,17 @@ cusadi_status batch_device(cusadi_batch b, BatchDev** out) {
   if (r != CUDA_SUCCESS) return bfail(CUSADI_E_CUDA, "cuModuleLoadData failed: " + std::to_string(r));
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  d.smem = (unsigned)b->coop_smem;
   for (int v = 0; v < kVariants; ++v) {
     std::string nm = "cs_batch_" + std::to_string(kBlocks[v]);
     if ((r = D.moduleGetFunction(&d.persist[v], d.mod, nm.c_str())) != CUDA_SUCCESS)
       return bfail(CUSADI_E_CUDA, "missing " + nm);
+    const unsigned smem = v == kCoopVariant ? d.smem : 0;
+    if (smem > 48 * 1024 &&
+        (r = D.funcSetAttribute(d.persist[v], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem)) != CUDA_SUCCESS)
+      return bfail(CUSADI_E_CUDA, "cuFuncSetAttribute failed: " + std::to_string(r));
     int per_sm = 0;
-    D.occupancy(&per_sm, d.persist[v], kBlocks[v], 0);
+    D.occupancy(&per_sm, d.persist[v], kBlocks[v], smem);
     const int64_t nt = (int64_t)b->tiles[v].size();
     d.grid[v] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), nt));
     size_t tb = std::max<size_t>(1, b->tiles[v].size()) * sizeof(BTile);
@@ -215,8 +258,8 @@ cusadi_status batch_device(cusadi_batch b, BatchDev** out) {
     cudaMemsetAsync(d.d_ticket, 0, sizeof(unsigned), d.cap);
     int nt = (int)b->tiles[v].size();
     void* args[] = {&d.d_tiles[v], &nt, &d.d_ticket, &d.d_args};
-    r = D.launchKernel(d.persist[v], (unsigned)d.grid[v], 1, 1, (unsigned)kBlocks[v], 1, 1, 0,
-                       (CUstream)d.cap, args, nullptr);
+    r = D.launchKernel(d.persist[v], (unsigned)d.grid[v], 1, 1, (unsigned)kBlocks[v], 1, 1,
+                       v == kCoopVariant ? d.smem : 0u, (CUstream)d.cap, args, nullptr);
     ce = cudaStreamEndCapture(d.cap, &g);
     if (r != CUDA_SUCCESS || ce != cudaSuccess)
       return bfail(CUSADI_E_CUDA, "capturing the batch launch failed");
@@ -251,6 +294,8 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
   for (int v = 0; v < kVariants; ++v)
     if (o.block == kBlocks[v]) b->variant = v;
   if (b->variant < 0) return bfail(CUSADI_E_INVALID_ARG, "batch block must be 32, 64 or 128");
+  if (o.ways != 0 && o.ways != kCoopWays)
+    return bfail(CUSADI_E_INVALID_ARG, "batch ways must be 0 or 4 (4 warps of the 128-thread scheduler)");
   b->progs.resize(n);
   const size_t elt_ws = o.dtype == CUSADI_F32 ? 4 : 8;
   try {
@@ -274,10 +319,18 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
       co.device_fn = true;
       co.prefix = "cs_b" + std::to_string(p);
       P.cg = generate(P.g, co);
+      P.coop = o.ways == kCoopWays && P.N <= kCoopMaxN && P.n_ops >= kCoopMinOps;
+      if (P.coop) {
+        CodegenOptions cc = co;
+        cc.prefix = "cs_bc" + std::to_string(p);
+        cc.coop_shared_kb = kCoopSharedKB;
+        P.ccg = generate_coop(P.g, cc, plan_coop(P.g, kCoopWays, 8.0));
+        b->coop_smem = std::max(b->coop_smem, P.ccg.smem_bytes);
+      }
       P.ldw = (P.N + 31) / 32 * 32;
       b->ws_bytes = (b->ws_bytes + 255) / 256 * 256;
       P.ws_off = b->ws_bytes;
-      b->ws_bytes += (size_t)P.cg.ws_rows * P.ldw * elt_ws;
+      b->ws_bytes += (size_t)std::max(P.cg.ws_rows, P.ccg.ws_rows) * P.ldw * elt_ws;
     }
   } catch (const std::bad_alloc&) {
     return bfail(CUSADI_E_OOM, "out of host memory");
@@ -291,6 +344,9 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
     P.bins.assign(P.cg.segs.size(), std::string());
     for (size_t s = 0; s < P.cg.segs.size(); ++s)
       jobs.push_back({&P.cg.segs[s].source, &P.cg.segs[s].name, &P.bins[s], "", false});
+    P.cbins.assign(P.ccg.segs.size(), std::string());
+    for (size_t s = 0; s < P.ccg.segs.size(); ++s)
+      jobs.push_back({&P.ccg.segs[s].source, &P.ccg.segs[s].name, &P.cbins[s], "", false});
   }
   jobs.push_back({&sched_src, &sched_name, &sched[0], "", false});
   std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo",
@@ -317,8 +373,10 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
   for (auto& j : jobs)
     if (!j.ok) return bfail(CUSADI_E_COMPILE, "NVRTC failed on " + *j.name + ": " + j.log.substr(0, 4000));
   std::vector<std::string> objs;
-  for (auto& P : b->progs)
+  for (auto& P : b->progs) {
     for (auto& x : P.bins) objs.push_back(x);
+    for (auto& x : P.cbins) objs.push_back(x);
+  }
   objs.push_back(sched[0]);
   std::string log;
   if (!link(objs, o, b->linked, log)) return bfail(CUSADI_E_COMPILE, "nvJitLink failed: " + log.substr(0, 4000));
@@ -327,9 +385,11 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
   std::iota(byops.begin(), byops.end(), 0);
   std::stable_sort(byops.begin(), byops.end(), [&](int a, int c) { return b->progs[a].n_ops > b->progs[c].n_ops; });
   for (int v = 0; v < kVariants; ++v) {
-    for (int p : byops)
-      for (int64_t f = 0; f < b->progs[p].N; f += kBlocks[v])
-        b->tiles[v].push_back({p, (int32_t)std::min<int64_t>(kBlocks[v], b->progs[p].N - f), f});
+    for (int p : byops) {
+      const int64_t t = v == kCoopVariant && b->progs[p].coop ? 32 : kBlocks[v];
+      for (int64_t f = 0; f < b->progs[p].N; f += t)
+        b->tiles[v].push_back({p, (int32_t)std::min<int64_t>(t, b->progs[p].N - f), f});
+    }
   }
   *out = b.release();
   return CUSADI_OK;

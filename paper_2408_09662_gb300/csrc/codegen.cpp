@@ -463,7 +463,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
   const bool sm64 = o.dtype != CUSADI_F32;
   // shared-memory budget for cross-warp values (CUSADI_COOP_SHARED_KB overrides
   // it, so tests can force the workspace overflow path on small programs)
-  int budget_kb = 160;
+  int budget_kb = o.coop_shared_kb;
   if (const char* e = std::getenv("CUSADI_COOP_SHARED_KB")) budget_kb = std::max(0, std::atoi(e));
   const int max_slots = (int)((budget_kb * 1024) / (32 * (sm64 ? 8 : 4)));
   const int n_slots = assign_coop_slots(g, plan, G.seg_of, max_slots, slot, gslot, n_gslots);
@@ -620,6 +620,32 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
       }
     }
     std::string name = o.prefix + "_" + std::to_string(s);
+    if (o.device_fn) {
+      // one group of 32 instances (first .. first + count - 1) per call, made
+      // by every thread of the calling CTA of 32 * W threads (the barriers
+      // need all of them); the barrier on entry orders this segment after the
+      // previous one's workspace writes and shared-slot reads
+      src << "extern \"C\" __device__ void " << name << "(\n"
+          << "    const " << tin << "* __restrict__ X, long long ldx, " << tin
+          << "* __restrict__ Y, long long ldy, " << tw << "* __restrict__ W, long long ldw,\n"
+          << "    long long first, int count, unsigned char* __restrict__ cs_smem) {\n"
+          << "  " << tsm << "* __restrict__ cs_x = reinterpret_cast<" << tsm << "*>(cs_smem);\n"
+          << "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n"
+          << "  const bool active = lane < count;\n"
+          << "  const long long i = first + (active ? lane : count - 1);\n"
+          << "  const " << tin << "* __restrict__ Xb = X;\n"
+          << "  X += i; Y += i; W += i;\n"
+          << "  (void)Xb; (void)W; (void)ldw; (void)cs_x;\n"
+          << "  __syncthreads();\n"
+          << regions.str() << "}\n";
+      Segment S;
+      S.begin = segs[s].first;
+      S.end = segs[s].second;
+      S.name = name;
+      S.source = src.str();
+      R.segs.push_back(std::move(S));
+      continue;
+    }
     src << "extern \"C\" __global__ void __launch_bounds__(" << 32 * W << ") " << name << "(\n"
         << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
         << "* __restrict__ X2, long long ldx2, " << tin << "* __restrict__ Y, long long ldy,\n    long long N, "

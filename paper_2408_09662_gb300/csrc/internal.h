@@ -106,6 +106,8 @@ struct CodegenOptions {
   bool adjoint = false;
   int64_t split = -1;            // input rows >= split come from the second buffer
   bool device_fn = false;        // emit relocatable __device__ functions of one instance
+                                 // (cooperative: of one group of 32, called by the whole CTA)
+  int coop_shared_kb = 160;      // shared memory for cross-warp values (cooperative)
   std::string prefix = "cs_fwd";
 };
 

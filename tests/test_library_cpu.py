@@ -308,6 +308,13 @@ def test_cooperative_kernels_reach_every_barrier(ways):
             L.cusadi_free(fn)
 
 
+def test_batch_ways_validated():
+    o = _opt(ways=2)
+    with pytest.raises(L.CusadiError) as e:
+        L.cusadi_batch_create([programs.listing2().to_bytes()], [16], o)
+    assert e.value.status == L.CUSADI_E_INVALID_ARG
+
+
 def test_cooperative_ways_validated():
     with pytest.raises(L.CusadiError):
         L.cusadi_load(programs.listing2().to_bytes(), _opt(ways=1))
