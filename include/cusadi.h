@@ -268,8 +268,11 @@ cusadi_status cusadi_densify(cusadi_fn fn, int arg, const void* y, int64_t ld_y,
  * 128-thread scheduler then runs such a program 32 instances per tile with
  * its 4 warps splitting the program between them (parallelism inside one
  * expression graph, which CusADi leaves to future work, §VI), so a long
- * program with few instances stops setting the length of the launch.
- * n <= 32.  Errors: INVALID_ARG, INVALID_IR, COMPILE, OOM. */
+ * program with few instances stops setting the length of the launch.  Such
+ * a program is compiled in cooperative form only: its plain launch (mode
+ * CUSADI_BATCH_PLAIN) runs the same code, 32 instances per 128-thread CTA,
+ * and the batch then runs 128-thread tiles only (cusadi_batch_set_block
+ * refuses 32 and 64).  n <= 32.  Errors: INVALID_ARG, INVALID_IR, COMPILE, OOM. */
 cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, const int64_t* N,
                                   int n, const cusadi_options* opt, cusadi_batch* out);
 void cusadi_batch_free(cusadi_batch b);
@@ -290,7 +293,8 @@ cusadi_status cusadi_batch_eval(cusadi_batch b, const void* const* in, const int
                                 int mode, cusadi_stream stream);
 
 /* Selects the tile size (32, 64 or 128 instances = threads per CTA) of the
- * persistent launch; the link holds all three. */
+ * persistent launch; the link holds all three.  INVALID_ARG for other sizes,
+ * and for 32 or 64 when the batch has cooperative programs (ways = 4). */
 cusadi_status cusadi_batch_set_block(cusadi_batch b, int block);
 
 /* Tile count, threads per CTA, persistent grid size (0 before the first

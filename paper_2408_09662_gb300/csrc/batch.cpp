@@ -65,7 +65,12 @@ struct BatchProg {
 // chains of the launch.
 constexpr int kCoopWays = 4;
 constexpr int kCoopVariant = 2;                  // the 128-thread scheduler
-constexpr int64_t kCoopMaxN = 8192, kCoopMinOps = 10000;
+// Which programs: at most N = 8192 instances and at least 60,000 ops, the
+// longest first, at most three and 450,000 ops in all.  The caps are measured:
+// nvJitLink (CUDA 13.0) failed inside nvJitLinkComplete when four programs of
+// 50k-200k ops were linked in cooperative form, while any three linked.
+constexpr int64_t kCoopMaxN = 8192, kCoopMinOps = 60000, kCoopMaxTotalOps = 450000;
+constexpr int kCoopMaxProgs = 3;
 constexpr int kCoopSharedKB = 96;
 
 struct BatchDev {
@@ -96,6 +101,7 @@ struct cusadi_batch_s {
   int variant = 2;
   size_t ws_bytes = 0;
   int64_t coop_smem = 0;         // largest shared-memory need of a cooperative program
+  bool has_coop = false;         // then only the 128-thread scheduler has tiles
   int registers = 0;
   std::mutex mu;
   std::map<int, BatchDev> dev;
@@ -140,6 +146,7 @@ std::string scheduler_source(const cusadi_batch_s& b) {
   s << "static __device__ __forceinline__ void cs_run(const BArg* __restrict__ A, int p, long long i) {\n"
     << "  switch (p) {\n";
   for (size_t p = 0; p < b.progs.size(); ++p) {
+    if (b.progs[p].coop) continue;
     s << "    case " << p << ": {\n      const BArg a = A[" << p << "];\n";
     for (auto& seg : b.progs[p].cg.segs)
       s << "      " << seg.name << "(a.X, a.ldx, a.X, a.ldx, a.Y, a.ldy, a.W, a.ldw, i);\n";
@@ -168,11 +175,17 @@ std::string scheduler_source(const cusadi_batch_s& b) {
       s << "    if ((int)threadIdx.x < tl.count) cs_run(A, tl.prog, tl.first + threadIdx.x);\n";
     s << "  }\n}\n";
   }
-  for (size_t p = 0; p < b.progs.size(); ++p)
+  for (size_t p = 0; p < b.progs.size(); ++p) {
     s << "extern \"C\" __global__ void __launch_bounds__(128) cs_plain_" << p
-      << "(const BArg* __restrict__ A, long long N) {\n"
-      << "  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n"
-      << "  if (i < N) cs_run(A, " << p << ", i);\n}\n";
+      << "(const BArg* __restrict__ A, long long N) {\n";
+    if (b.progs[p].coop)   // one group of 32 instances per CTA of 4 warps
+      s << "  extern __shared__ __align__(16) unsigned char cs_dyn[];\n"
+        << "  const long long first = (long long)blockIdx.x * 32;\n"
+        << "  cs_run_coop(A, " << p << ", first, (int)(N - first < 32 ? N - first : 32), cs_dyn);\n}\n";
+    else
+      s << "  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n"
+        << "  if (i < N) cs_run(A, " << p << ", i);\n}\n";
+  }
   return s.str();
 }
 
@@ -244,6 +257,9 @@ cusadi_status batch_device(cusadi_batch b, BatchDev** out) {
     std::string nm = "cs_plain_" + std::to_string(p);
     if ((r = D.moduleGetFunction(&d.plain[p], d.mod, nm.c_str())) != CUDA_SUCCESS)
       return bfail(CUSADI_E_CUDA, "missing " + nm);
+    if (b->progs[p].coop && d.smem > 48 * 1024 &&
+        (r = D.funcSetAttribute(d.plain[p], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)d.smem)) != CUDA_SUCCESS)
+      return bfail(CUSADI_E_CUDA, "cuFuncSetAttribute failed: " + std::to_string(r));
   }
   if ((ce = cudaMalloc((void**)&d.d_ticket, 256)) != cudaSuccess) return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
   if ((ce = cudaMalloc((void**)&d.d_args, kMaxProgs * sizeof(BArg))) != cudaSuccess)
@@ -311,6 +327,24 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
       if (o.schedule) schedule(P.g);
       P.n_ops = count_ops(P.g);
       P.N = N[p];
+    }
+    if (o.ways == kCoopWays) {
+      std::vector<int> cand;
+      for (int p = 0; p < n; ++p)
+        if (b->progs[p].N <= kCoopMaxN && b->progs[p].n_ops >= kCoopMinOps) cand.push_back(p);
+      std::stable_sort(cand.begin(), cand.end(),
+                       [&](int a, int c) { return b->progs[a].n_ops > b->progs[c].n_ops; });
+      int64_t total = 0;
+      int taken = 0;
+      for (int p : cand)
+        if (taken < kCoopMaxProgs && total + b->progs[p].n_ops <= kCoopMaxTotalOps) {
+          b->progs[p].coop = true;
+          total += b->progs[p].n_ops;
+          ++taken;
+        }
+    }
+    for (int p = 0; p < n; ++p) {
+      BatchProg& P = b->progs[p];
       CodegenOptions co;
       co.dtype = o.dtype;
       co.segment_ops = o.segment_ops;
@@ -318,9 +352,11 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
       co.own_math = o.own_math != 0;
       co.device_fn = true;
       co.prefix = "cs_b" + std::to_string(p);
-      P.cg = generate(P.g, co);
-      P.coop = o.ways == kCoopWays && P.N <= kCoopMaxN && P.n_ops >= kCoopMinOps;
+      // a cooperative program is linked in cooperative form only
+      if (!P.coop) P.cg = generate(P.g, co);
       if (P.coop) {
+        b->has_coop = true;
+        b->variant = kCoopVariant;
         CodegenOptions cc = co;
         cc.prefix = "cs_bc" + std::to_string(p);
         cc.coop_shared_kb = kCoopSharedKB;
@@ -385,6 +421,7 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
   std::iota(byops.begin(), byops.end(), 0);
   std::stable_sort(byops.begin(), byops.end(), [&](int a, int c) { return b->progs[a].n_ops > b->progs[c].n_ops; });
   for (int v = 0; v < kVariants; ++v) {
+    if (b->has_coop && v != kCoopVariant) continue;
     for (int p : byops) {
       const int64_t t = v == kCoopVariant && b->progs[p].coop ? 32 : kBlocks[v];
       for (int64_t f = 0; f < b->progs[p].N; f += t)
@@ -418,6 +455,8 @@ cusadi_status cusadi_batch_set_block(cusadi_batch b, int block) {
   if (!b) return bfail(CUSADI_E_INVALID_ARG, "NULL batch");
   for (int v = 0; v < kVariants; ++v)
     if (block == kBlocks[v]) {
+      if (b->has_coop && v != kCoopVariant)
+        return bfail(CUSADI_E_INVALID_ARG, "a batch with cooperative programs runs 128-thread tiles only");
       b->variant = v;
       return CUSADI_OK;
     }
@@ -461,8 +500,9 @@ cusadi_status cusadi_batch_eval(cusadi_batch b, const void* const* in, const int
   for (size_t p = 0; p < n; ++p) {
     long long N = b->progs[p].N;
     void* a[] = {&d->d_args, &N};
-    CUresult r = driver().launchKernel(d->plain[p], (unsigned)((N + 127) / 128), 1, 1, 128, 1, 1, 0,
-                                       (CUstream)st, a, nullptr);
+    const bool coop = b->progs[p].coop;
+    CUresult r = driver().launchKernel(d->plain[p], (unsigned)(coop ? (N + 31) / 32 : (N + 127) / 128),
+                                       1, 1, 128, 1, 1, coop ? d->smem : 0u, (CUstream)st, a, nullptr);
     if (r != CUDA_SUCCESS) return bfail(CUSADI_E_CUDA, "cuLaunchKernel failed: " + std::to_string(r));
   }
   return CUSADI_OK;
