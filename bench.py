@@ -321,9 +321,10 @@ def other_configs(dev, pk64, pk32, flush, reps):
         "op_instances_generated": gen_ops, "persistent_ms": ms_p, "plain_8_launches_ms": ms_s,
         "speedup_persistent_vs_plain": ms_s / ms_p, "tile_block": block,
         "persistent_ms_by_tile_block": {str(k): v for k, v in by_block.items()},
-        "cooperative_tiles": "ways=4: programs with N <= 8192 and >= 10,000 ops run 32 instances "
-                             "per 128-thread tile, 4 warps splitting the program; their plain "
-                             "launch is the same cooperative code", **b.info(),
+        "cooperative_tiles": "ways=4: the longest programs with N <= 8192 and >= 60,000 ops (at most "
+                             "three; here 100k, 150k, 200k) run 32 instances per 128-thread tile, "
+                             "4 warps splitting the program; their plain launch runs the same "
+                             "cooperative code", **b.info(),
         "gop_per_s_generated": gen_ops / (ms_p * 1e-3) * 1e-9, "setup_seconds": t_compile}
     return out
 

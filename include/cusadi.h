@@ -264,7 +264,9 @@ cusadi_status cusadi_densify(cusadi_fn fn, int arg, const void* y, int64_t ld_y,
  * instances each.  opt: dtype, block (32, 64 or 128: instances per tile),
  * maxrregcount, fmad, schedule, segment_ops, compile_threads, cache_dir;
  * path and compile_limit_ops are ignored (always compiled).  ways: 0, or 4 to
- * give programs with N[j] <= 8192 and >= 10,000 ops cooperative tiles: the
+ * give the longest programs with N[j] <= 8192 and >= 60,000 ops (at most
+ * three, 450,000 ops in all: larger sets made nvJitLink fail) cooperative
+ * tiles: the
  * 128-thread scheduler then runs such a program 32 instances per tile with
  * its 4 warps splitting the program between them (parallelism inside one
  * expression graph, which CusADi leaves to future work, §VI), so a long
