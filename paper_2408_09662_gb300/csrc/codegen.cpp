@@ -253,6 +253,12 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     R.ws_rows = rows;
   }
   for (uint8_t f : g.out_reduce) R.has_reduce |= (f != 0);
+  std::vector<int64_t> reduce_k(g.out_reduce.size(), -1);
+  for (size_t r = 0; r < g.out_reduce.size(); ++r)
+    if (g.out_reduce[r]) {
+      reduce_k[r] = (int64_t)R.reduce_rows.size();
+      R.reduce_rows.push_back((int64_t)r);
+    }
 
   const char* tin = G.buf_f64() ? "double" : "float";
   const char* tw = G.ws_f64() ? "double" : "float";
@@ -289,14 +295,17 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     auto store_out = [&](int64_t r, const std::string& v) {
       if (o.adjoint) {
         if (g.out_reduce[r]) {
-          body << "  if (reduce) {\n    " << tin << " r_ = active ? (" << tin << ")" << v
-               << " : (" << tin << ")0;\n"
+          // warp sum (fixed shuffle order), written by lane 0 as the warp's
+          // partial; a warp whose lane 0 is past N has no instance at all
+          body << "  if (reduce) {\n    " << tw << " r_ = active ? (" << tw << ")" << v
+               << " : (" << tw << ")0;\n"
                << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 16);\n"
                << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 8);\n"
                << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 4);\n"
                << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 2);\n"
                << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 1);\n"
-               << "    if ((threadIdx.x & 31u) == 0u) atomicAdd(&Yb[" << r << "ll * ldy], r_);\n"
+               << "    if ((threadIdx.x & 31u) == 0u && i0 < N) Wp[" << reduce_k[r]
+               << "ll * ((N + 31) >> 5) + (i0 >> 5)] = r_;\n"
                << "  } else if (active) { " << tin << "* p_ = &Y[" << r << "ll * ldy]; *p_ = acc ? *p_ + ("
                << tin << ")" << v << " : (" << tin << ")" << v << "; }\n";
         } else {
@@ -381,8 +390,10 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     }
     src << "  const " << tin << "* __restrict__ Xb = X;\n"
         << "  const " << tin << "* __restrict__ X2b = X2;\n"
-        << "  " << tin << "* __restrict__ Yb = Y;\n"
-        << "  X += i; X2 += i; Y += i; W += i;\n"
+        << "  " << tin << "* __restrict__ Yb = Y;\n";
+    if (o.adjoint && R.has_reduce)
+      src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw;  // warp partials\n";
+    src << "  X += i; X2 += i; Y += i; W += i;\n"
         << "  (void)Xb; (void)X2b; (void)Yb; (void)W; (void)ldw; (void)ldx2; (void)acc; (void)reduce; (void)active;\n"
         << body.str() << "}\n";
     Segment S;
@@ -393,14 +404,32 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     R.segs.push_back(std::move(S));
   }
   if (R.has_reduce) {
-    // clears the reduced rows (column 0) before an overwriting adjoint
+    // one CTA per reduced row adds the warp partials in a fixed order (strided
+    // per thread, then a tree), so the sum is the same on every run; it then
+    // writes, or adds to, the row's column 0
     std::ostringstream z;
-    R.zero_kernel = o.prefix + "_zero";
-    z << "extern \"C\" __global__ void " << R.zero_kernel << "(" << tin << "* Y, long long ldy) {\n"
-      << "  if (blockIdx.x != 0 || threadIdx.x != 0) return;\n";
-    for (size_t r = 0; r < g.out_reduce.size(); ++r)
-      if (g.out_reduce[r]) z << "  Y[" << r << "ll * ldy] = (" << tin << ")0;\n";
-    z << "}\n";
+    R.finish_kernel = o.prefix + "_finish";
+    z << "static __device__ const long long cs_reduce_row[] = {";
+    for (size_t k = 0; k < R.reduce_rows.size(); ++k) z << (k ? ", " : "") << R.reduce_rows[k];
+    z << "};\n"
+      << "extern \"C\" __global__ void __launch_bounds__(256) " << R.finish_kernel << "(const " << tw
+      << "* __restrict__ W, long long ldw, long long N, " << tin << "* __restrict__ Y, long long ldy, "
+      << "int accumulate) {\n"
+      << "  __shared__ " << tw << " s_[256];\n"
+      << "  const long long nw = (N + 31) >> 5;\n"
+      << "  const " << tw << "* __restrict__ P = W + " << R.ws_rows << "ll * ldw + (long long)blockIdx.x * nw;\n"
+      << "  " << tw << " a = 0;\n"
+      << "  for (long long w = threadIdx.x; w < nw; w += 256) a += P[w];\n"
+      << "  s_[threadIdx.x] = a;\n"
+      << "  __syncthreads();\n"
+      << "  for (int d = 128; d > 0; d >>= 1) {\n"
+      << "    if ((int)threadIdx.x < d) s_[threadIdx.x] += s_[threadIdx.x + d];\n"
+      << "    __syncthreads();\n"
+      << "  }\n"
+      << "  if (threadIdx.x == 0) {\n"
+      << "    " << tin << "* p = &Y[cs_reduce_row[blockIdx.x] * ldy];\n"
+      << "    *p = (" << tin << ")(accumulate ? (" << tw << ")*p + s_[0] : s_[0]);\n"
+      << "  }\n}\n";
     R.segs[0].source += z.str();
   }
   return R;

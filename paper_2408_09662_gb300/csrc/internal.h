@@ -92,7 +92,11 @@ struct CodegenResult {
   std::vector<Segment> segs;
   int64_t ws_rows = 0;           // workspace rows (values carried between segments)
   bool has_reduce = false;
-  std::string zero_kernel;       // name of the kernel that clears reduced rows
+  // reduced rows (adjoint): each warp writes its partial sum to workspace row
+  // ws_rows + k, column = warp index (leading dimension ceil(N / 32)); the
+  // finish kernel adds the partials in a fixed order
+  std::vector<int64_t> reduce_rows;
+  std::string finish_kernel;
   int coop_ways = 0;             // > 0: cooperative kernels, 32 * coop_ways threads per CTA
   int64_t smem_bytes = 0;        // dynamic shared memory per CTA (cooperative kernels)
 };

@@ -149,7 +149,7 @@ struct DevState {
   int sms = 0;                       // streaming multiprocessors of the device
   std::vector<CUmodule> mods;
   std::vector<CUfunction> fwd, adj;
-  CUfunction adj_zero = nullptr;
+  CUfunction adj_finish = nullptr;   // fixed-order sum of the reduced rows' warp partials
   void* d_ops_fwd = nullptr;
   double* d_k_fwd = nullptr;
   void* d_ops_adj = nullptr;
@@ -337,7 +337,7 @@ cusadi_status load_on_device(cusadi_fn fn, DevState& ds, bool adjoint) {
       }
       fs.push_back(f);
       if (s == 0 && adjoint && d.cg.has_reduce) {
-        r = driver().moduleGetFunction(&ds.adj_zero, m, d.cg.zero_kernel.c_str());
+        r = driver().moduleGetFunction(&ds.adj_finish, m, d.cg.finish_kernel.c_str());
         if (r != CUDA_SUCCESS) return cuda_fail("cuModuleGetFunction", r);
       }
     }
@@ -372,7 +372,9 @@ size_t direction_ws(cusadi_fn fn, const Direction& d, int64_t N) {
     if (interp_block(d.ip.n_slots, fn->opt.dtype) > 0) return 0;
     return (size_t)d.ip.n_slots * interp_ldw(N) * elt_ws(fn->opt.dtype);
   }
-  return (size_t)d.cg.ws_rows * round_up(N, 32) * elt_ws(fn->opt.dtype);
+  // rows carried between kernels, then (adjoint) one partial per warp and reduced row
+  return ((size_t)d.cg.ws_rows * round_up(N, 32) + d.cg.reduce_rows.size() * (size_t)((N + 31) / 32)) *
+         elt_ws(fn->opt.dtype);
 }
 
 bool all_bcast(const Graph& g, int64_t rows) {
@@ -826,24 +828,27 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
   const int acc = (flags & CUSADI_ADJ_ACCUMULATE) ? 1 : 0;
   const bool has_reduce = fn->path == CUSADI_PATH_INTERP ? fn->adj.ip.has_reduce : fn->adj.cg.has_reduce;
   const bool acc_bcast = acc || (flags & CUSADI_ADJ_ACCUMULATE_BROADCAST);
-  if (reduce && !acc_bcast && has_reduce) {
-    if (fn->path == CUSADI_PATH_INTERP) {
-      // clear column 0 of the broadcast rows
-      const size_t e = elt_io(fn->opt.dtype);
-      for (int64_t r = 0; r < fn->ir.nnz_in; ++r) {
-        if (!fn->fwd.g.in_bcast[r]) continue;
-        cudaError_t ce = cudaMemsetAsync((char*)in_bar + (size_t)r * ld_ib * e, 0, e, (cudaStream_t)stream);
-        if (ce != cudaSuccess) return cuda_fail("cudaMemsetAsync", ce);
-      }
-    } else {
-      long long ly = ld_ib;
-      void* args[] = {&in_bar, &ly};
-      CUresult r = driver().launchKernel(ds->adj_zero, 1, 1, 1, 32, 1, 1, 0, (CUstream)stream, args, nullptr);
-      if (r != CUDA_SUCCESS) return cuda_fail("cuLaunchKernel", r);
+  if (reduce && !acc_bcast && has_reduce && fn->path == CUSADI_PATH_INTERP) {
+    // the interpreter adds warp sums with atomics: clear column 0 of the broadcast rows
+    const size_t e = elt_io(fn->opt.dtype);
+    for (int64_t r = 0; r < fn->ir.nnz_in; ++r) {
+      if (!fn->fwd.g.in_bcast[r]) continue;
+      cudaError_t ce = cudaMemsetAsync((char*)in_bar + (size_t)r * ld_ib * e, 0, e, (cudaStream_t)stream);
+      if (ce != cudaSuccess) return cuda_fail("cudaMemsetAsync", ce);
     }
   }
-  return run(fn, fn->adj, *ds, true, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, workspace, acc,
-             reduce ? 1 : 0, stream);
+  s = run(fn, fn->adj, *ds, true, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, workspace, acc,
+          reduce ? 1 : 0, stream);
+  if (s != CUSADI_OK || !reduce || !has_reduce || fn->path == CUSADI_PATH_INTERP) return s;
+  // compiled path: the kernels left one partial per warp and reduced row in
+  // the workspace; sum them in a fixed order (the same bits on every run)
+  long long lw = round_up(N, 32), n = N, ly = ld_ib;
+  int accumulate = acc_bcast ? 1 : 0;
+  void* args[] = {&workspace, &lw, &n, &in_bar, &ly, &accumulate};
+  CUresult r = driver().launchKernel(ds->adj_finish, (unsigned)fn->adj.cg.reduce_rows.size(), 1, 1, 256, 1, 1,
+                                     0, (CUstream)stream, args, nullptr);
+  if (r != CUDA_SUCCESS) return cuda_fail("cuLaunchKernel", r);
+  return CUSADI_OK;
 }
 
 cusadi_status cusadi_stream_wait(cusadi_stream stream, double timeout_seconds) {
