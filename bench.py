@@ -181,6 +181,7 @@ def other_configs(dev, pk64, pk32, flush, reps):
            "c3f64": pool.submit(Function, ir3, dtype="f64"),
            "c3mixed": pool.submit(Function, ir3, dtype="mixed"),
            "srbf64": pool.submit(Function, srb, dtype="f64", adjoint=1),
+           "srbf64w8": pool.submit(Function, srb, dtype="f64", adjoint=1, ways=8),
            "srbf32": pool.submit(Function, srb, dtype="f32", adjoint=1)}
     pool.shutdown(wait=True)   # nothing is timed while host threads compile
     fut = {k: f.result() for k, f in fut.items()}
@@ -273,6 +274,18 @@ def other_configs(dev, pk64, pk32, flush, reps):
             "forward_ms": ms_f, "adjoint_ms": ms_a, "adjoint_forward_ratio": ms_a / ms_f,
             "forward_roofline_frac": peaks.roofline_seconds(fn, pk64, pk32) * Nk / (ms_f * 1e-3),
             "adjoint_roofline_frac": peaks.roofline_seconds(fn, pk64, pk32, adjoint=True) * Nk / (ms_a * 1e-3)}
+    # FP64 with 8 warps per 32 instances (cooperative forward and adjoint kernels)
+    prog = StepProgram(fut["srbf64w8"], 144, 12)
+    x0 = torch.tensor(x0n, device=dev, requires_grad=True)
+    K = torch.tensor(Kn.reshape(144), device=dev, requires_grad=True)
+    fwd = _events_ms(lambda: rollout(prog, x0.detach(), K.detach(), 50), reps, flush)
+
+    def fbc():
+        L, _ = rollout(prog, x0, K, 50)
+        L.backward()
+    both = _events_ms(fbc, reps, flush)
+    rec["f64_ways8"] = {"forward_ms": fwd, "backward_ms": both - fwd,
+                        "adjoint_forward_ratio": (both - fwd) / fwd}
     out["srb_rollout"] = rec
 
     # --- f1 LQR closed-loop step (SDA Riccati solve inside), N = 10,000, FP64 ---

@@ -197,6 +197,9 @@ std::string op_expr(Gen& G, const Node& x, bool f, const std::string& A, const s
 
 }  // namespace
 
+std::string finish_source(CodegenResult& R, const std::string& prefix, const char* tin,
+                          const char* tw);
+
 CodegenResult generate(const Graph& g, const CodegenOptions& o) {
   CodegenResult R;
   Gen G(g, o);
@@ -403,12 +406,18 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     S.source = src.str();
     R.segs.push_back(std::move(S));
   }
-  if (R.has_reduce) {
-    // one CTA per reduced row adds the warp partials in a fixed order (strided
-    // per thread, then a tree), so the sum is the same on every run; it then
-    // writes, or adds to, the row's column 0
+  if (R.has_reduce) R.segs[0].source += finish_source(R, o.prefix, tin, tw);
+  return R;
+}
+
+// One CTA per reduced row adds the warp partials in a fixed order (strided per
+// thread, then a tree), so the sum is the same on every run; it then writes,
+// or adds to, the row's column 0.
+std::string finish_source(CodegenResult& R, const std::string& prefix, const char* tin,
+                          const char* tw) {
+  {
     std::ostringstream z;
-    R.finish_kernel = o.prefix + "_finish";
+    R.finish_kernel = prefix + "_finish";
     z << "static __device__ const long long cs_reduce_row[] = {";
     for (size_t k = 0; k < R.reduce_rows.size(); ++k) z << (k ? ", " : "") << R.reduce_rows[k];
     z << "};\n"
@@ -430,9 +439,8 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
       << "    " << tin << "* p = &Y[cs_reduce_row[blockIdx.x] * ldy];\n"
       << "    *p = (" << tin << ")(accumulate ? (" << tw << ")*p + s_[0] : s_[0]);\n"
       << "  }\n}\n";
-    R.segs[0].source += z.str();
+    return z.str();
   }
-  return R;
 }
 
 }  // namespace cusadi
@@ -528,6 +536,35 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
   const char* tw = G.ws_f64() ? "double" : "float";
   const bool sm_f64 = sm64;  // shared slots hold the widest type in use
   const char* tsm = sm_f64 ? "double" : "float";
+  // adjoint outputs: accumulate or overwrite; a reduced (broadcast) row's sum
+  // over the group's 32 instances is the group's partial (column blockIdx.x)
+  for (uint8_t f : g.out_reduce) R.has_reduce |= (f != 0);
+  std::vector<int64_t> reduce_k(g.out_reduce.size(), -1);
+  for (size_t r = 0; r < g.out_reduce.size(); ++r)
+    if (g.out_reduce[r]) {
+      reduce_k[r] = (int64_t)R.reduce_rows.size();
+      R.reduce_rows.push_back((int64_t)r);
+    }
+  auto store_out = [&](std::ostringstream& body, int64_t r, const std::string& v) {
+    if (!o.adjoint) {
+      body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
+      return;
+    }
+    const std::string plain = std::string("if (active) { ") + tin + "* p_ = &Y[" + std::to_string(r) +
+                              "ll * ldy]; *p_ = acc ? *p_ + (" + tin + ")" + v + " : (" + tin + ")" + v + "; }";
+    if (!g.out_reduce[r]) {
+      body << "    " << plain << "\n";
+      return;
+    }
+    body << "    if (reduce) {\n      " << tw << " r_ = active ? (" << tw << ")" << v << " : (" << tw << ")0;\n"
+         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 16);\n"
+         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 8);\n"
+         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 4);\n"
+         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 2);\n"
+         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 1);\n"
+         << "      if (lane == 0) Wp[" << reduce_k[r] << "ll * ((N + 31) >> 5) + blockIdx.x] = r_;\n"
+         << "    } else " << plain << "\n";
+  };
   // nodes per (segment, warp, phase) in topological order
   for (int s = 0; s < nseg; ++s) {
     std::vector<std::vector<std::vector<int64_t>>> work(W, std::vector<std::vector<int64_t>>(segs[s].second - segs[s].first));
@@ -572,7 +609,11 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
             lhs = std::string("    const ") + G.ty(f) + " " + name;
           }
           if (x.op == INPUT) {
-            body << lhs << " = (" << G.ty(f) << ")" << (x.bcast ? "Xb[" : "X[") << x.io << "ll * ldx];\n";
+            const bool second = o.split >= 0 && x.io >= o.split;   // adjoint: y_bar rows
+            const int64_t row = second ? x.io - o.split : x.io;
+            body << lhs << " = (" << G.ty(f) << ")"
+                 << (second ? (x.bcast ? "X2b[" : "X2[") : (x.bcast ? "Xb[" : "X[")) << row
+                 << (second ? "ll * ldx2];\n" : "ll * ldx];\n");
           } else if (G.seg_of[i] != s) {
             body << lhs << " = (" << G.ty(f) << ")W[" << G.ws_slot[i] << "ll * ldw];\n";
           } else if (plan.owner[i] != w) {
@@ -605,8 +646,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
           if (slot[i] >= 0) body << "    cs_x[" << slot[i] << " * 32 + lane] = (" << tsm << ")v" << i << ";\n";
           if (gslot[i] >= 0) body << "    if (active) W[" << g_base + gslot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
           if (G.ws_slot[i] >= 0) body << "    if (active) W[" << G.ws_slot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
-          for (int64_t r : G.out_rows[i])
-            body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")v" << i << ";\n";
+          for (int64_t r : G.out_rows[i]) store_out(body, r, "v" + std::to_string(i));
         }
         phase_warp[q][w] = body.str();
         body.str("");
@@ -617,7 +657,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
         for (int64_t i = 0; i < n; ++i) {
           if (!G.leaf(i) || G.out_rows[i].empty()) continue;
           std::string v = operand((int32_t)i, G.node_f64((int32_t)i));
-          for (int64_t r : G.out_rows[i]) body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
+          for (int64_t r : G.out_rows[i]) store_out(body, r, v);
         }
       }
       if (!body.str().empty()) phase_warp[nph - 1][w] += body.str();
@@ -686,8 +726,10 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
         << "  const bool active = i0 < N;\n"
         << "  const long long i = active ? i0 : N - 1;\n"
         << "  const " << tin << "* __restrict__ Xb = X;\n"
-        << "  X += i; Y += i; W += i;\n"
-        << "  (void)Xb; (void)X2; (void)ldx2; (void)W; (void)ldw; (void)acc; (void)reduce; (void)cs_x;\n"
+        << "  const " << tin << "* __restrict__ X2b = X2;\n";
+    if (R.has_reduce) src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw;  // group partials\n";
+    src << "  X += i; X2 += i; Y += i; W += i;\n"
+        << "  (void)Xb; (void)X2b; (void)ldx2; (void)W; (void)ldw; (void)acc; (void)reduce; (void)cs_x;\n"
         << regions.str() << "}\n";
     Segment S;
     S.begin = segs[s].first;
@@ -698,6 +740,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
   }
   R.coop_ways = W;
   R.smem_bytes = (int64_t)std::max(n_slots, 1) * 32 * (sm_f64 ? 8 : 4);
+  if (R.has_reduce && !o.device_fn) R.segs[0].source += finish_source(R, o.prefix, tin, tw);
   return R;
 }
 

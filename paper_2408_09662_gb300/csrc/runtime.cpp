@@ -220,8 +220,9 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.split = adjoint ? fn->ir.nnz_in : -1;
   static const char* tag[] = {"f64", "f32", "mixed"};
   co.prefix = std::string(adjoint ? "cs_adj_" : "cs_fwd_") + tag[fn->opt.dtype];
-  if (fn->opt.ways > 1 && !adjoint) {
-    co.prefix = std::string("cs_coop") + std::to_string(fn->opt.ways) + "_" + tag[fn->opt.dtype];
+  if (fn->opt.ways > 1) {
+    co.prefix = std::string(adjoint ? "cs_coopadj" : "cs_coop") + std::to_string(fn->opt.ways) + "_" +
+                tag[fn->opt.dtype];
     CoopPlan plan = plan_coop(d.g, fn->opt.ways, 8.0);
     d.cg = generate_coop(d.g, co, plan);
     if (d.cg.smem_bytes > 200 * 1024)   // cannot happen: overflow goes to the workspace

@@ -56,3 +56,47 @@ def test_coop_mpc_mixed_and_lqr():
                    rng.uniform(0.5, 10, (6, 500)), rng.uniform(0.05, 0.5, (1, 500))])
     for ways in (4, 6, 8):
         _check(lqr, Z, Function(lqr, dtype="f64", ways=ways), 1e-12, 0)
+
+
+@pytest.mark.parametrize("ways", [4, 8])
+def test_cooperative_adjoint_equals_plain_adjoint(ways):
+    """The SRB step's adjoint split over W warps per 32 instances: with FMA
+    contraction off every op rounds once in either layout, and a group of 32
+    instances is a warp in both, so the per-instance rows and the 144 reduced
+    gain rows (per-group partials, fixed-order finish) agree bit for bit with
+    the one-thread-per-instance adjoint, for every flag combination."""
+    ir = programs.srb_step().to_bytes()
+    a = Function(ir, dtype="f64", fmad=0, adjoint=1)
+    b = Function(ir, dtype="f64", fmad=0, adjoint=1, ways=ways)
+    N = 4100
+    rng = np.random.default_rng(50 + ways)
+    X = np.vstack([np.tile(rng.normal(0, 0.1, (144, 1)), (1, N)), rng.uniform(-0.1, 0.1, (12, N)),
+                   np.zeros((1, N))])
+    x = torch.tensor(X, device="cuda")
+    ybar = torch.tensor(rng.normal(0, 1, (13, N)), device="cuda")
+    for kw in (dict(), dict(reduce_broadcast=True), dict(accumulate=True),
+               dict(reduce_broadcast=True, accumulate_broadcast=True)):
+        outs = []
+        for fn in (a, b):
+            o = torch.ones((157, N), dtype=torch.float64, device="cuda")
+            fn.adjoint(x, ybar, out=o, **kw)
+            outs.append(o)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[0], outs[1]), kw
+
+
+def test_cooperative_rollout_gradient_equals_plain():
+    from paper_2408_09662_gb300.rollout import StepProgram, rollout
+    ir = programs.srb_step().to_bytes()
+    res = []
+    for ways in (0, 8):
+        prog = StepProgram(Function(ir, dtype="f64", fmad=0, adjoint=1, ways=ways), 144, 12)
+        rng = np.random.default_rng(60)
+        x0 = torch.tensor(rng.uniform(-0.1, 0.1, (12, 2048)), device="cuda", requires_grad=True)
+        K = torch.tensor(rng.normal(0, 0.1, 144), device="cuda", requires_grad=True)
+        L, xT = rollout(prog, x0, K, 20)
+        L.backward()
+        res.append((L.item(), xT.detach().cpu(), x0.grad.cpu(), K.grad.cpu()))
+    assert res[0][0] == res[1][0]
+    for u, v in zip(res[0][1:], res[1][1:]):
+        assert torch.equal(u, v)

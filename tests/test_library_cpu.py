@@ -286,12 +286,22 @@ def test_cooperative_kernels_reach_every_barrier(ways):
     from shared memory or the workspace was written by its owner in an earlier
     phase and not overwritten before the read."""
     import re as _re
-    for ir in (programs.cartpole_rk4(), programs.random_program(3000, seed=ways)):
+
+    def sources(fn):
+        for adjoint in (False, True):      # the adjoint kernels are cooperative too
+            seg = 0
+            while True:
+                try:
+                    yield L.cusadi_source(fn, adjoint, seg)
+                except L.CusadiError:
+                    break
+                seg += 1
+    for ir in (programs.cartpole_rk4(), programs.random_program(3000, seed=ways), programs.srb_step()):
         fn = L.cusadi_load(ir.to_bytes(), _opt(ways=ways, segment_ops=1200))
         try:
-            for seg in range(L.cusadi_info(fn).n_segments):
-                src = L.cusadi_source(fn, False, seg)
-                body = src[src.index("if (warp =="):]
+            for src in sources(fn):
+                # the cooperative kernel (an adjoint's fixed-order finishing kernel follows it)
+                body = src[src.index("if (warp =="):].split("static __device__ const long long cs_reduce_row")[0]
                 assert "barrier.sync" not in src and "return" not in body
                 for line in body.splitlines():
                     if "__syncthreads" in line:
