@@ -150,7 +150,8 @@ cusadi_status cusadi_op_counts(cusadi_fn fn, int which, int64_t* counts, int n);
 
 /* Bytes of device workspace one evaluation of N instances needs: rows for
  * values carried between the kernels of a long program, and for the adjoint
- * one partial sum per warp of every broadcast row (0 when neither applies).
+ * one row of per-instance terms for every broadcast input (0 when neither
+ * applies).
  * The caller allocates it, 256-byte aligned. */
 size_t cusadi_workspace_bytes(cusadi_fn fn, int64_t N, int adjoint);
 
@@ -168,8 +169,8 @@ cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out
 /* Reverse mode: in_bar = J(x)^T out_bar per instance, J = d out / d in.
  * out_bar: [nnz_out x ld_ob]; in_bar: [nnz_in x ld_ib].  With
  * CUSADI_ADJ_REDUCE_BROADCAST, broadcast input rows receive the sum over
- * instances in column 0: on the compiled path each warp writes its partial
- * sum to the workspace and a second kernel adds the partials in a fixed
+ * instances in column 0: on the compiled path each instance writes its term
+ * to the workspace and a second kernel adds each row's terms in a fixed
  * order, so the result has the same bits on every run; the interpreter path
  * adds warp sums with atomics (order, and last bits, vary).  Without the flag
  * they receive per-instance values.

@@ -298,17 +298,10 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     auto store_out = [&](int64_t r, const std::string& v) {
       if (o.adjoint) {
         if (g.out_reduce[r]) {
-          // warp sum (fixed shuffle order), written by lane 0 as the warp's
-          // partial; a warp whose lane 0 is past N has no instance at all
-          body << "  if (reduce) {\n    " << tw << " r_ = active ? (" << tw << ")" << v
-               << " : (" << tw << ")0;\n"
-               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 16);\n"
-               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 8);\n"
-               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 4);\n"
-               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 2);\n"
-               << "    r_ += __shfl_xor_sync(0xffffffffu, r_, 1);\n"
-               << "    if ((threadIdx.x & 31u) == 0u && i0 < N) Wp[" << reduce_k[r]
-               << "ll * ((N + 31) >> 5) + (i0 >> 5)] = r_;\n"
+          // the instance's term goes to the workspace (a coalesced store); the
+          // finishing kernel sums each such row over the instances
+          body << "  if (reduce) {\n    if (active) Wp[" << reduce_k[r] << "ll * ldw] = (" << tw << ")" << v
+               << ";\n"
                << "  } else if (active) { " << tin << "* p_ = &Y[" << r << "ll * ldy]; *p_ = acc ? *p_ + ("
                << tin << ")" << v << " : (" << tin << ")" << v << "; }\n";
         } else {
@@ -395,7 +388,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
         << "  const " << tin << "* __restrict__ X2b = X2;\n"
         << "  " << tin << "* __restrict__ Yb = Y;\n";
     if (o.adjoint && R.has_reduce)
-      src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw;  // warp partials\n";
+      src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw + i;  // reduced-row terms\n";
     src << "  X += i; X2 += i; Y += i; W += i;\n"
         << "  (void)Xb; (void)X2b; (void)Yb; (void)W; (void)ldw; (void)ldx2; (void)acc; (void)reduce; (void)active;\n"
         << body.str() << "}\n";
@@ -410,9 +403,9 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
   return R;
 }
 
-// One CTA per reduced row adds the warp partials in a fixed order (strided per
-// thread, then a tree), so the sum is the same on every run; it then writes,
-// or adds to, the row's column 0.
+// One CTA per reduced row adds the row's N per-instance terms in a fixed order
+// (strided per thread, then a tree), so the sum is the same on every run; it
+// then writes, or adds to, the row's column 0.
 std::string finish_source(CodegenResult& R, const std::string& prefix, const char* tin,
                           const char* tw) {
   {
@@ -421,17 +414,16 @@ std::string finish_source(CodegenResult& R, const std::string& prefix, const cha
     z << "static __device__ const long long cs_reduce_row[] = {";
     for (size_t k = 0; k < R.reduce_rows.size(); ++k) z << (k ? ", " : "") << R.reduce_rows[k];
     z << "};\n"
-      << "extern \"C\" __global__ void __launch_bounds__(256) " << R.finish_kernel << "(const " << tw
+      << "extern \"C\" __global__ void __launch_bounds__(512) " << R.finish_kernel << "(const " << tw
       << "* __restrict__ W, long long ldw, long long N, " << tin << "* __restrict__ Y, long long ldy, "
       << "int accumulate) {\n"
-      << "  __shared__ " << tw << " s_[256];\n"
-      << "  const long long nw = (N + 31) >> 5;\n"
-      << "  const " << tw << "* __restrict__ P = W + " << R.ws_rows << "ll * ldw + (long long)blockIdx.x * nw;\n"
+      << "  __shared__ " << tw << " s_[512];\n"
+      << "  const " << tw << "* __restrict__ P = W + (" << R.ws_rows << "ll + blockIdx.x) * ldw;\n"
       << "  " << tw << " a = 0;\n"
-      << "  for (long long w = threadIdx.x; w < nw; w += 256) a += P[w];\n"
+      << "  for (long long j = threadIdx.x; j < N; j += 512) a += P[j];\n"
       << "  s_[threadIdx.x] = a;\n"
       << "  __syncthreads();\n"
-      << "  for (int d = 128; d > 0; d >>= 1) {\n"
+      << "  for (int d = 256; d > 0; d >>= 1) {\n"
       << "    if ((int)threadIdx.x < d) s_[threadIdx.x] += s_[threadIdx.x + d];\n"
       << "    __syncthreads();\n"
       << "  }\n"
@@ -536,8 +528,8 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
   const char* tw = G.ws_f64() ? "double" : "float";
   const bool sm_f64 = sm64;  // shared slots hold the widest type in use
   const char* tsm = sm_f64 ? "double" : "float";
-  // adjoint outputs: accumulate or overwrite; a reduced (broadcast) row's sum
-  // over the group's 32 instances is the group's partial (column blockIdx.x)
+  // adjoint outputs: accumulate or overwrite; a reduced (broadcast) row's term
+  // goes to its workspace row, summed over the instances by the finishing kernel
   for (uint8_t f : g.out_reduce) R.has_reduce |= (f != 0);
   std::vector<int64_t> reduce_k(g.out_reduce.size(), -1);
   for (size_t r = 0; r < g.out_reduce.size(); ++r)
@@ -556,14 +548,8 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
       body << "    " << plain << "\n";
       return;
     }
-    body << "    if (reduce) {\n      " << tw << " r_ = active ? (" << tw << ")" << v << " : (" << tw << ")0;\n"
-         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 16);\n"
-         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 8);\n"
-         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 4);\n"
-         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 2);\n"
-         << "      r_ += __shfl_xor_sync(0xffffffffu, r_, 1);\n"
-         << "      if (lane == 0) Wp[" << reduce_k[r] << "ll * ((N + 31) >> 5) + blockIdx.x] = r_;\n"
-         << "    } else " << plain << "\n";
+    body << "    if (reduce) { if (active) Wp[" << reduce_k[r] << "ll * ldw] = (" << tw << ")" << v
+         << "; } else " << plain << "\n";
   };
   // nodes per (segment, warp, phase) in topological order
   for (int s = 0; s < nseg; ++s) {
@@ -727,7 +713,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
         << "  const long long i = active ? i0 : N - 1;\n"
         << "  const " << tin << "* __restrict__ Xb = X;\n"
         << "  const " << tin << "* __restrict__ X2b = X2;\n";
-    if (R.has_reduce) src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw;  // group partials\n";
+    if (R.has_reduce) src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw + i;  // reduced-row terms\n";
     src << "  X += i; X2 += i; Y += i; W += i;\n"
         << "  (void)Xb; (void)X2b; (void)ldx2; (void)W; (void)ldw; (void)acc; (void)reduce; (void)cs_x;\n"
         << regions.str() << "}\n";

@@ -92,9 +92,9 @@ struct CodegenResult {
   std::vector<Segment> segs;
   int64_t ws_rows = 0;           // workspace rows (values carried between segments)
   bool has_reduce = false;
-  // reduced rows (adjoint): each warp writes its partial sum to workspace row
-  // ws_rows + k, column = warp index (leading dimension ceil(N / 32)); the
-  // finish kernel adds the partials in a fixed order
+  // reduced rows (adjoint): each instance writes its term to workspace row
+  // ws_rows + k (instance-indexed columns); the finish kernel adds each row's
+  // terms in a fixed order
   std::vector<int64_t> reduce_rows;
   std::string finish_kernel;
   int coop_ways = 0;             // > 0: cooperative kernels, 32 * coop_ways threads per CTA

@@ -149,7 +149,7 @@ struct DevState {
   int sms = 0;                       // streaming multiprocessors of the device
   std::vector<CUmodule> mods;
   std::vector<CUfunction> fwd, adj;
-  CUfunction adj_finish = nullptr;   // fixed-order sum of the reduced rows' warp partials
+  CUfunction adj_finish = nullptr;   // fixed-order sum of the reduced rows' per-instance terms
   void* d_ops_fwd = nullptr;
   double* d_k_fwd = nullptr;
   void* d_ops_adj = nullptr;
@@ -373,9 +373,8 @@ size_t direction_ws(cusadi_fn fn, const Direction& d, int64_t N) {
     if (interp_block(d.ip.n_slots, fn->opt.dtype) > 0) return 0;
     return (size_t)d.ip.n_slots * interp_ldw(N) * elt_ws(fn->opt.dtype);
   }
-  // rows carried between kernels, then (adjoint) one partial per warp and reduced row
-  return ((size_t)d.cg.ws_rows * round_up(N, 32) + d.cg.reduce_rows.size() * (size_t)((N + 31) / 32)) *
-         elt_ws(fn->opt.dtype);
+  // rows carried between kernels, then (adjoint) one row of per-instance terms per reduced row
+  return ((size_t)d.cg.ws_rows + d.cg.reduce_rows.size()) * round_up(N, 32) * elt_ws(fn->opt.dtype);
 }
 
 bool all_bcast(const Graph& g, int64_t rows) {
@@ -841,12 +840,12 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
   s = run(fn, fn->adj, *ds, true, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, workspace, acc,
           reduce ? 1 : 0, stream);
   if (s != CUSADI_OK || !reduce || !has_reduce || fn->path == CUSADI_PATH_INTERP) return s;
-  // compiled path: the kernels left one partial per warp and reduced row in
+  // compiled path: the kernels left each reduced row's per-instance terms in
   // the workspace; sum them in a fixed order (the same bits on every run)
   long long lw = round_up(N, 32), n = N, ly = ld_ib;
   int accumulate = acc_bcast ? 1 : 0;
   void* args[] = {&workspace, &lw, &n, &in_bar, &ly, &accumulate};
-  CUresult r = driver().launchKernel(ds->adj_finish, (unsigned)fn->adj.cg.reduce_rows.size(), 1, 1, 256, 1, 1,
+  CUresult r = driver().launchKernel(ds->adj_finish, (unsigned)fn->adj.cg.reduce_rows.size(), 1, 1, 512, 1, 1,
                                      0, (CUstream)stream, args, nullptr);
   if (r != CUDA_SUCCESS) return cuda_fail("cuLaunchKernel", r);
   return CUSADI_OK;

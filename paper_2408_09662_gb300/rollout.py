@@ -8,8 +8,8 @@ t % 2 and writes the state rows of the other.
 Backward pass (reverse mode through the library's adjoint kernels): states are
 kept every ``checkpoint_every`` steps; each segment is recomputed forward from
 its checkpoint, then the adjoint kernel runs once per step in reverse.  The
-parameter gradient is reduced over instances by the adjoint (warp shuffles,
-one partial per warp, a fixed-order sum of the partials) and accumulated over
+parameter gradient is reduced over instances by the adjoint (per-instance
+terms in the workspace, summed in a fixed order) and accumulated over
 steps in place, so it has the same bits on every run.
 """
 from __future__ import annotations

@@ -61,10 +61,10 @@ def test_coop_mpc_mixed_and_lqr():
 @pytest.mark.parametrize("ways", [4, 8])
 def test_cooperative_adjoint_equals_plain_adjoint(ways):
     """The SRB step's adjoint split over W warps per 32 instances: with FMA
-    contraction off every op rounds once in either layout, and a group of 32
-    instances is a warp in both, so the per-instance rows and the 144 reduced
-    gain rows (per-group partials, fixed-order finish) agree bit for bit with
-    the one-thread-per-instance adjoint, for every flag combination."""
+    contraction off every op rounds once in either layout, so the per-instance
+    rows and the 144 reduced gain rows agree bit for bit with
+    the one-thread-per-instance adjoint, for every flag combination (the
+    reduced rows' per-instance terms are summed by the same finishing kernel)."""
     ir = programs.srb_step().to_bytes()
     a = Function(ir, dtype="f64", fmad=0, adjoint=1)
     b = Function(ir, dtype="f64", fmad=0, adjoint=1, ways=ways)

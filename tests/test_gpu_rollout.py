@@ -140,8 +140,8 @@ def test_graph_replayed_rollout_matches_eager(prog64):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_shared_gain_reduction_is_reproducible(dtype):
-    """The 144 broadcast rows summed over 65,536 instances (2,048 warp
-    partials each): repeated adjoints give the same bits, with and without
+    """The 144 broadcast rows summed over 65,536 instances: repeated adjoints
+    give the same bits, with and without
     accumulation, and the sum matches a float64 sum of the per-instance
     adjoints (reduce_broadcast off) to rounding."""
     fn = Function(programs.srb_step(), dtype=dtype, adjoint=1)
@@ -162,5 +162,5 @@ def test_shared_gain_reduction_is_reproducible(dtype):
         np.allclose(c[:144, 0].double().cpu().numpy(), 2 * a[:144, 0].double().cpu().numpy(), rtol=1e-6)
     want = per[:144].double().sum(dim=1).cpu().numpy()
     got = a[:144, 0].double().cpu().numpy()
-    tol = (1e-12 if dtype == "f64" else 2e-5) * np.abs(per[:144].double()).sum(dim=1).cpu().numpy()
+    tol = (1e-12 if dtype == "f64" else 2e-5) * per[:144].double().abs().sum(dim=1).cpu().numpy()
     assert np.all(np.abs(got - want) <= tol)

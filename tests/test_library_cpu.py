@@ -220,12 +220,11 @@ def test_adjoint_source_generates_reduction_for_broadcast_inputs():
     fn = L.cusadi_load(ir.to_bytes(), _opt())
     try:
         src = L.cusadi_source(fn, adjoint=True)
-        # rows 2 and 3 are the reduced rows 0 and 1: one partial per warp, no atomics
-        assert "__shfl_xor_sync" in src and "atomicAdd" not in src
-        assert "Wp[0ll * ((N + 31) >> 5) + (i0 >> 5)]" in src
-        assert "Wp[1ll * ((N + 31) >> 5) + (i0 >> 5)]" in src
+        # rows 2 and 3 are the reduced rows 0 and 1: per-instance terms, no atomics
+        assert "atomicAdd" not in src and "__shfl" not in src
+        assert "Wp[0ll * ldw]" in src and "Wp[1ll * ldw]" in src
         assert "cs_reduce_row[] = {2, 3}" in src and "cs_adj_f64_finish" in src
-        assert L.cusadi_workspace_bytes(fn, 1000, True) == 2 * 32 * 8   # 2 rows x 32 warps
+        assert L.cusadi_workspace_bytes(fn, 1000, True) == 2 * 1024 * 8   # 2 rows x round_up(N, 32)
         assert L.cusadi_workspace_bytes(fn, 1000, False) == 0
         assert L.cusadi_info(fn).n_bcast_in == 2
         counts = L.cusadi_op_counts(fn, adjoint=True)
