@@ -157,7 +157,8 @@ def test_shared_gain_reduction_is_reproducible(dtype):
     fn.adjoint(x, ybar, out=c, reduce_broadcast=True, accumulate_broadcast=True)
     per = fn.adjoint(x, ybar)
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    # written entries only: column 0 of the reduced rows, every column of the others
+    assert torch.equal(a[:144, 0], b[:144, 0]) and torch.equal(a[144:], b[144:])
     assert torch.equal(c[:144, 0], (a[:144, 0].double() * 2).to(fn.torch_dtype)) or \
         np.allclose(c[:144, 0].double().cpu().numpy(), 2 * a[:144, 0].double().cpu().numpy(), rtol=1e-6)
     want = per[:144].double().sum(dim=1).cpu().numpy()
