@@ -5,6 +5,7 @@ markdown table.
     python -m paper_2408_09662_gb300.experiments coop   # within-instance parallelism (§VI)
     python -m paper_2408_09662_gb300.experiments mpc    # MPC cost/violation vs iterations (§V-A, Fig. 4)
     python -m paper_2408_09662_gb300.experiments one random20k f64 4096 8   # one kernel, for a profiler
+    python -m paper_2408_09662_gb300.experiments one srb f64 65536 0 adjoint
 
 ldlt: LDL^T solves of SPD systems, each about ten times the operations of the
 previous one, timed on the same inputs by the engine (compiled, or the
@@ -202,19 +203,26 @@ def mpc_pareto(N=4096, steps=100, Ms=(1, 2, 3, 5, 8), warm_Ms=(1, 2), dtype="f64
     return rows
 
 
-def one_kernel(program="random20k", dtype="f64", N=4096, ways=0, reps=3):
-    """Compile one program and launch it `reps` times (a small case for a profiler)."""
+def one_kernel(program="random20k", dtype="f64", N=4096, ways=0, reps=3, adjoint=False):
+    """Compile one program and launch it `reps` times (a small case for a
+    profiler); adjoint: its reverse sweep (broadcast rows reduced) instead."""
     irs = {"random20k": lambda: programs.random_program(20000, seed=0),
            "cartpole": programs.cartpole_rk4, "mpc": programs.quadrotor_mpc,
            "lqr": programs.quadrotor_lqr_step, "srb": programs.srb_step}
-    fn = Function(irs[program]().to_bytes(), dtype=dtype, ways=ways)
-    x = torch.tensor(inputs.normal(fn.nnz_in, N, seed=1), dtype=fn.torch_dtype, device="cuda")
+    fn = Function(irs[program]().to_bytes(), dtype=dtype, ways=ways, adjoint=int(adjoint))
+    x = torch.tensor(inputs.normal(fn.nnz_in, N, seed=1) * 0.1, dtype=fn.torch_dtype, device="cuda")
     y = fn(x)
+    if adjoint:
+        ybar = torch.ones_like(y)
+        xbar = fn.adjoint(x, ybar, reduce_broadcast=True)
+        run = lambda: fn.adjoint(x, ybar, out=xbar, reduce_broadcast=True)   # noqa: E731
+    else:
+        run = lambda: fn(x, out=y)                                           # noqa: E731
     for _ in range(reps):
-        fn(x, out=y)
+        run()
     torch.cuda.synchronize()
-    print(f"{program} {dtype} N={N} ways={ways}: {fn.info.n_segments} kernel(s), "
-          f"{_gpu_ms(lambda: fn(x, out=y)):.4f} ms")
+    print(f"{program} {dtype} N={N} ways={ways}{' adjoint' if adjoint else ''}: "
+          f"{fn.info.n_segments} forward kernel(s), {_gpu_ms(run):.4f} ms")
 
 
 def main(argv):
@@ -226,9 +234,9 @@ def main(argv):
     elif which == "mpc":
         mpc_pareto()
     elif which == "one":
-        # one <program> <dtype> <N> <ways>
+        # one <program> <dtype> <N> <ways> [adjoint]
         prog, dt, N, w = (argv[2:] + ["random20k", "f64", "4096", "0"][len(argv) - 2:])[:4]
-        one_kernel(prog, dt, int(N), int(w))
+        one_kernel(prog, dt, int(N), int(w), adjoint="adjoint" in argv[6:])
     else:
         print(__doc__)
         return 2
