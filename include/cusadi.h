@@ -169,11 +169,10 @@ cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out
 /* Reverse mode: in_bar = J(x)^T out_bar per instance, J = d out / d in.
  * out_bar: [nnz_out x ld_ob]; in_bar: [nnz_in x ld_ib].  With
  * CUSADI_ADJ_REDUCE_BROADCAST, broadcast input rows receive the sum over
- * instances in column 0: on the compiled path each instance writes its term
- * to the workspace and a second kernel adds each row's terms in a fixed
- * order, so the result has the same bits on every run; the interpreter path
- * adds warp sums with atomics (order, and last bits, vary).  Without the flag
- * they receive per-instance values.
+ * instances in column 0: each instance writes its term to the workspace and
+ * a second kernel adds each row's terms in a fixed order, so the result has
+ * the same bits on every run (compiled and interpreter paths alike).  Without
+ * the flag they receive per-instance values.
  * Without CUSADI_ADJ_ACCUMULATE the written entries are overwritten, except the
  * reduced rows under CUSADI_ADJ_ACCUMULATE_BROADCAST (gradient accumulation of
  * a shared parameter over many calls, e.g. the steps of a rollout).

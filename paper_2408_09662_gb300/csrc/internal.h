@@ -148,6 +148,7 @@ struct InterpProgram {
   std::vector<uint8_t> in_bcast;
   int64_t n_slots = 0;
   bool has_reduce = false;
+  std::vector<int64_t> reduce_rows;   // output rows summed over instances (adjoint)
 };
 
 bool pack_interp(const Graph& g, InterpProgram& p, std::string& err);
@@ -157,7 +158,11 @@ bool pack_interp(const Graph& g, InterpProgram& p, std::string& err);
 int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, const void* X,
                   int64_t ldx, const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy,
                   int64_t N, void* W, int64_t ldw, int64_t n_slots, int acc, int reduce,
-                  void* stream);
+                  void* Wr, int64_t ldr, void* stream);
+// fixed-order sums of the reduced rows' per-instance terms (row k of Wr, k <
+// n_rows) into column 0 of output rows rows[k]
+int launch_reduce_finish(int dtype, const void* Wr, int64_t ldr, int64_t N, const int64_t* rows,
+                         int64_t n_rows, void* Y, int64_t ldy, int accumulate, void* stream);
 // threads per block of the shared-memory interpreter (0: work vector too long)
 int interp_block(int64_t n_slots, int dtype);
 // dense copy of one output argument (kernels.cu); returns a cudaError_t value

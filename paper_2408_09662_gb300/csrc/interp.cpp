@@ -50,7 +50,12 @@ bool pack_interp(const Graph& g, InterpProgram& p, std::string& err) {
   auto emit_outputs = [&](int64_t i) -> bool {
     for (int64_t r : out_rows[i]) {
       if ((uint64_t)r > AUX_MAX) { err = "too many output rows for the interpreter"; return false; }
-      uint32_t red = (!g.out_reduce.empty() && g.out_reduce[r]) ? 1u : 0u;
+      // a reduced (broadcast) row carries its index among the reduced rows + 1
+      uint32_t red = 0;
+      if (!g.out_reduce.empty() && g.out_reduce[r]) {
+        p.reduce_rows.push_back(r);
+        red = (uint32_t)p.reduce_rows.size();
+      }
       p.has_reduce |= red != 0;
       p.ops.push_back({code(OUTPUT, 0, (uint64_t)r), 0, (uint32_t)slot[i], red});
     }

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) interp_kernel(
     const uint4* __restrict__ ops, long long n_ops, const double* __restrict__ K,
     const B* __restrict__ X, long long ldx, const B* __restrict__ X2, long long ldx2,
     long long split, B* __restrict__ Y, long long ldy, long long N, S* __restrict__ W,
-    long long ldw, int acc, int reduce) {
+    long long ldw, int acc, int reduce, S* __restrict__ Wr, long long ldr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i0 < N;
@@ -95,10 +95,8 @@ __global__ void __launch_bounds__(256) interp_kernel(
     }
     if (op == OUTPUT) {
       B v = (B)w[o.z * ws];
-      if (o.w && reduce) {
-        B r = active ? v : B(0);
-        for (int d = 16; d > 0; d >>= 1) r += __shfl_xor_sync(0xffffffffu, r, d);
-        if ((threadIdx.x & 31u) == 0u) atomicAdd(&Y[aux * ldy], r);
+      if (o.w && reduce) {   // reduced row o.w - 1: the instance's term, summed later
+        if (active) Wr[(long long)(o.w - 1) * ldr + i0] = w[o.z * ws];
       } else if (active) {
         B* p = &Y[aux * ldy + i0];
         *p = acc ? *p + v : v;
@@ -120,7 +118,8 @@ __global__ void __launch_bounds__(256) interp_kernel(
 template <typename B, typename S, bool MIXED, bool SMEM>
 int launch(const IOp* ops, int64_t n_ops, const double* k, const void* X, int64_t ldx,
            const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy, int64_t N, void* W,
-           int64_t ldw, int64_t n_slots, int block, int acc, int reduce, cudaStream_t st) {
+           int64_t ldw, int64_t n_slots, int block, int acc, int reduce, void* Wr, int64_t ldr,
+           cudaStream_t st) {
   auto kern = interp_kernel<B, S, MIXED, SMEM>;
   size_t smem = SMEM ? (size_t)n_slots * block * sizeof(S) : 0;
   if (smem > 48 * 1024) {
@@ -130,8 +129,30 @@ int launch(const IOp* ops, int64_t n_ops, const double* k, const void* X, int64_
   long long grid = (N + block - 1) / block;
   kern<<<(unsigned)grid, block, smem, st>>>(reinterpret_cast<const uint4*>(ops), n_ops, k,
                                             (const B*)X, ldx, (const B*)X2, ldx2, split, (B*)Y,
-                                            ldy, N, (S*)W, ldw, acc, reduce);
+                                            ldy, N, (S*)W, ldw, acc, reduce, (S*)Wr, ldr);
   return (int)cudaGetLastError();
+}
+
+// One CTA per reduced row: strided per-thread sums, then a tree, always in the
+// same order, so the result has the same bits on every run.
+template <typename B, typename S>
+__global__ void __launch_bounds__(512) reduce_finish_kernel(const S* __restrict__ Wr, long long ldr,
+                                                            long long N, const int64_t* __restrict__ rows,
+                                                            B* __restrict__ Y, long long ldy, int accumulate) {
+  __shared__ S s_[512];
+  const S* __restrict__ P = Wr + (long long)blockIdx.x * ldr;
+  S a = 0;
+  for (long long j = threadIdx.x; j < N; j += 512) a += P[j];
+  s_[threadIdx.x] = a;
+  __syncthreads();
+  for (int d = 256; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) s_[threadIdx.x] += s_[threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    B* p = &Y[rows[blockIdx.x] * ldy];
+    *p = (B)(accumulate ? (S)*p + s_[0] : s_[0]);
+  }
 }
 
 }  // namespace
@@ -148,19 +169,19 @@ int interp_block(int64_t n_slots, int dtype) {
 int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, const void* X,
                   int64_t ldx, const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy,
                   int64_t N, void* W, int64_t ldw, int64_t n_slots, int acc, int reduce,
-                  void* stream) {
+                  void* Wr, int64_t ldr, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   int b = interp_block(n_slots, dtype);
   const bool smem = b > 0;
   if (!smem) b = 128;
   if (dtype == CUSADI_F64)
-    return smem ? launch<double, double, false, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st)
-                : launch<double, double, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st);
+    return smem ? launch<double, double, false, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st)
+                : launch<double, double, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st);
   if (dtype == CUSADI_F32)
-    return smem ? launch<float, float, false, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st)
-                : launch<float, float, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st);
-  return smem ? launch<float, double, true, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st)
-              : launch<float, double, true, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, st);
+    return smem ? launch<float, float, false, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st)
+                : launch<float, float, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st);
+  return smem ? launch<float, double, true, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st)
+              : launch<float, double, true, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st);
 }
 
 // Dense copy of one sparse output argument: dense[k * ldd + i] = y[(off +
@@ -193,6 +214,22 @@ int launch_densify(int dtype, const void* y, int64_t ldy, int64_t off, const int
   else
     densify_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((const float*)y, ldy, off, map, n_dense,
                                                           (float*)dense, ldd, N);
+  return (int)cudaGetLastError();
+}
+
+int launch_reduce_finish(int dtype, const void* Wr, int64_t ldr, int64_t N, const int64_t* rows,
+                         int64_t n_rows, void* Y, int64_t ldy, int accumulate, void* stream) {
+  if (n_rows <= 0 || N <= 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == CUSADI_F64)
+    reduce_finish_kernel<double, double><<<(unsigned)n_rows, 512, 0, st>>>(
+        (const double*)Wr, ldr, N, rows, (double*)Y, ldy, accumulate);
+  else if (dtype == CUSADI_F32)
+    reduce_finish_kernel<float, float><<<(unsigned)n_rows, 512, 0, st>>>(
+        (const float*)Wr, ldr, N, rows, (float*)Y, ldy, accumulate);
+  else
+    reduce_finish_kernel<float, double><<<(unsigned)n_rows, 512, 0, st>>>(
+        (const double*)Wr, ldr, N, rows, (float*)Y, ldy, accumulate);
   return (int)cudaGetLastError();
 }
 

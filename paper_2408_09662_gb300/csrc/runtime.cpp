@@ -154,6 +154,7 @@ struct DevState {
   double* d_k_fwd = nullptr;
   void* d_ops_adj = nullptr;
   double* d_k_adj = nullptr;
+  int64_t* d_reduce_rows = nullptr;  // interpreter adjoint: rows summed over instances
   // host-buffer evaluation: a copy-in and a copy-out stream, one compute
   // stream per chunk, and the events that order them (created on first use)
   cudaStream_t h_in = nullptr, h_out = nullptr;
@@ -318,6 +319,11 @@ cusadi_status load_on_device(cusadi_fn fn, DevState& ds, bool adjoint) {
     if ((ce = cudaMalloc((void**)&k, kb)) != cudaSuccess) { cudaFree(ops); return cuda_fail("cudaMalloc", ce); }
     if (!d.ip.ops.empty()) cudaMemcpy(ops, d.ip.ops.data(), d.ip.ops.size() * sizeof(IOp), cudaMemcpyHostToDevice);
     if (!d.ip.k.empty()) cudaMemcpy(k, d.ip.k.data(), d.ip.k.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (adjoint && !d.ip.reduce_rows.empty()) {
+      const size_t rb = d.ip.reduce_rows.size() * sizeof(int64_t);
+      if ((ce = cudaMalloc((void**)&ds.d_reduce_rows, rb)) != cudaSuccess) return cuda_fail("cudaMalloc", ce);
+      cudaMemcpy(ds.d_reduce_rows, d.ip.reduce_rows.data(), rb, cudaMemcpyHostToDevice);
+    }
     if ((ce = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail("upload", ce);
     (adjoint ? ds.d_ops_adj : ds.d_ops_fwd) = ops;
     (adjoint ? ds.d_k_adj : ds.d_k_fwd) = k;
@@ -369,10 +375,9 @@ int64_t interp_ldw(int64_t N) { return round_up(std::max<int64_t>(N, 1), 128); }
 
 size_t direction_ws(cusadi_fn fn, const Direction& d, int64_t N) {
   if (N <= 0) return 0;
-  if (fn->path == CUSADI_PATH_INTERP) {
-    if (interp_block(d.ip.n_slots, fn->opt.dtype) > 0) return 0;
-    return (size_t)d.ip.n_slots * interp_ldw(N) * elt_ws(fn->opt.dtype);
-  }
+  if (fn->path == CUSADI_PATH_INTERP)   // global work slots (if any), then reduced-row terms
+    return ((interp_block(d.ip.n_slots, fn->opt.dtype) > 0 ? 0 : (size_t)d.ip.n_slots * interp_ldw(N)) +
+            d.ip.reduce_rows.size() * (size_t)round_up(N, 32)) * elt_ws(fn->opt.dtype);
   // rows carried between kernels, then (adjoint) one row of per-instance terms per reduced row
   return ((size_t)d.cg.ws_rows + d.cg.reduce_rows.size()) * round_up(N, 32) * elt_ws(fn->opt.dtype);
 }
@@ -389,10 +394,15 @@ cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const 
                   int64_t ldx, const void* X2, int64_t ldx2, void* Y, int64_t ldy, int64_t N,
                   void* W, int acc, int reduce, cusadi_stream stream, int64_t ldw = 0) {
   if (fn->path == CUSADI_PATH_INTERP) {
+    const int64_t lw = ldw > 0 ? ldw : interp_ldw(N);
+    void* Wr = (W && !d.ip.reduce_rows.empty())
+                   ? (void*)((char*)W + (interp_block(d.ip.n_slots, fn->opt.dtype) > 0 ? 0 : (size_t)d.ip.n_slots * lw) *
+                                            elt_ws(fn->opt.dtype))
+                   : nullptr;
     int rc = launch_interp((const IOp*)(adjoint ? ds.d_ops_adj : ds.d_ops_fwd),
                            (int64_t)d.ip.ops.size(), adjoint ? ds.d_k_adj : ds.d_k_fwd,
                            fn->opt.dtype, X, ldx, X2 ? X2 : X, ldx2, adjoint ? fn->ir.nnz_in : (int64_t)1 << 40,
-                           Y, ldy, N, W, ldw > 0 ? ldw : interp_ldw(N), d.ip.n_slots, acc, reduce, stream);
+                           Y, ldy, N, W, lw, d.ip.n_slots, acc, reduce, Wr, round_up(N, 32), stream);
     if (rc != 0) return fail(CUSADI_E_CUDA, std::string("interpreter launch: ") + cudaGetErrorString((cudaError_t)rc));
     return CUSADI_OK;
   }
@@ -564,6 +574,7 @@ void cusadi_free(cusadi_fn fn) {
       if (ds.d_k_fwd) cudaFree(ds.d_k_fwd);
       if (ds.d_ops_adj) cudaFree(ds.d_ops_adj);
       if (ds.d_k_adj) cudaFree(ds.d_k_adj);
+      if (ds.d_reduce_rows) cudaFree(ds.d_reduce_rows);
       if (ds.h_in) cudaStreamDestroy(ds.h_in);
       if (ds.h_out) cudaStreamDestroy(ds.h_out);
       for (cudaStream_t st : ds.h_comp) cudaStreamDestroy(st);
@@ -828,20 +839,20 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
   const int acc = (flags & CUSADI_ADJ_ACCUMULATE) ? 1 : 0;
   const bool has_reduce = fn->path == CUSADI_PATH_INTERP ? fn->adj.ip.has_reduce : fn->adj.cg.has_reduce;
   const bool acc_bcast = acc || (flags & CUSADI_ADJ_ACCUMULATE_BROADCAST);
-  if (reduce && !acc_bcast && has_reduce && fn->path == CUSADI_PATH_INTERP) {
-    // the interpreter adds warp sums with atomics: clear column 0 of the broadcast rows
-    const size_t e = elt_io(fn->opt.dtype);
-    for (int64_t r = 0; r < fn->ir.nnz_in; ++r) {
-      if (!fn->fwd.g.in_bcast[r]) continue;
-      cudaError_t ce = cudaMemsetAsync((char*)in_bar + (size_t)r * ld_ib * e, 0, e, (cudaStream_t)stream);
-      if (ce != cudaSuccess) return cuda_fail("cudaMemsetAsync", ce);
-    }
-  }
   s = run(fn, fn->adj, *ds, true, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, workspace, acc,
           reduce ? 1 : 0, stream);
-  if (s != CUSADI_OK || !reduce || !has_reduce || fn->path == CUSADI_PATH_INTERP) return s;
-  // compiled path: the kernels left each reduced row's per-instance terms in
-  // the workspace; sum them in a fixed order (the same bits on every run)
+  if (s != CUSADI_OK || !reduce || !has_reduce) return s;
+  // the kernels left each reduced row's per-instance terms in the workspace;
+  // sum them in a fixed order (the same bits on every run)
+  if (fn->path == CUSADI_PATH_INTERP) {
+    const InterpProgram& ip = fn->adj.ip;
+    const size_t off = (interp_block(ip.n_slots, fn->opt.dtype) > 0 ? 0 : (size_t)ip.n_slots * interp_ldw(N)) *
+                       elt_ws(fn->opt.dtype);
+    int rc = launch_reduce_finish(fn->opt.dtype, (char*)workspace + off, round_up(N, 32), N, ds->d_reduce_rows,
+                                  (int64_t)ip.reduce_rows.size(), in_bar, ld_ib, acc_bcast ? 1 : 0, stream);
+    if (rc != 0) return fail(CUSADI_E_CUDA, std::string("reduction launch: ") + cudaGetErrorString((cudaError_t)rc));
+    return CUSADI_OK;
+  }
   long long lw = round_up(N, 32), n = N, ly = ld_ib;
   int accumulate = acc_bcast ? 1 : 0;
   void* args[] = {&workspace, &lw, &n, &in_bar, &ly, &accumulate};
