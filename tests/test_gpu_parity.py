@@ -256,17 +256,25 @@ def test_autograd_through_function():
 
 def test_stream_wait_times_out_then_completes():
     """A bounded wait: a long evaluation is still running after 1 ms (TIMEOUT,
-    work left running), and a second wait with a generous limit sees it finish."""
+    work left running), and a second wait with a generous limit sees it finish.
+    Garbage collection is kept out of the window: freeing an earlier test's
+    function (cudaFree, module unload) would synchronise the device."""
+    import gc
     from paper_2408_09662_gb300 import _lib as L
     ir = programs.random_program(20000, seed=0).to_bytes()
     fn = Function(ir, dtype="f64")
     x = torch.tensor(inputs.normal(64, 65536, seed=1), device="cuda")
     y = fn(x)
+    gc.collect()
     torch.cuda.synchronize()
     s = torch.cuda.current_stream().cuda_stream
-    fn(x, out=y)
-    with pytest.raises(L.CusadiError) as e:
-        L.cusadi_stream_wait(s, 0.001)
+    gc.disable()
+    try:
+        fn(x, out=y)
+        with pytest.raises(L.CusadiError) as e:
+            L.cusadi_stream_wait(s, 0.001)
+    finally:
+        gc.enable()
     assert e.value.status == L.CUSADI_E_TIMEOUT
     L.cusadi_stream_wait(s, 60.0)
 
