@@ -410,6 +410,10 @@ def main():
                     help="skip the cart-pole / MPC / rollout / batch measurements")
     ap.add_argument("--only", choices=["both", "f64", "f32"], default="both",
                     help="time one kernel only (for profiling); prints no JSON line")
+    ap.add_argument("--ways64", default="auto",
+                    help="warps per 32 instances of the FP64 kernel: auto (fastest of 0, 2, 4), or a number")
+    ap.add_argument("--ways32", default="auto",
+                    help="warps per 32 instances of the FP32 kernel: auto (fastest of 0, 2, 4), or a number")
     ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc"],
                     help="run one of the paper's experiments instead (markdown table, no JSON line); "
                          "ldlt adds the CPU oracle as its CPU baseline column")
@@ -442,18 +446,43 @@ def main():
     from paper_2408_09662_gb300.api import Function
 
     ir = programs.random_program(N_OPS_GEN, seed=PROGRAM_SEED).to_bytes()
-    with ThreadPoolExecutor(2) as ex:   # the two NVRTC compiles overlap (ctypes drops the GIL)
-        f64_fut = ex.submit(Function, ir, dtype="f64")
-        f32_fut = ex.submit(Function, ir, dtype="f32")
-        fn64, fn32 = f64_fut.result(), f32_fut.result()
+    # launch configuration: one thread per instance (ways 0) or W warps sharing each
+    # group of 32 instances (cooperative kernels); "auto" times the candidates once
+    # and keeps the fastest, as Batch.tune does for the tile size
+    cand = {"f64": [0, 2, 4] if args.ways64 == "auto" else [int(args.ways64)],
+            "f32": [0, 2, 4] if args.ways32 == "auto" else [int(args.ways32)]}
+    with ThreadPoolExecutor(6) as ex:   # the NVRTC compiles overlap (ctypes drops the GIL)
+        futs = {(dt, w): ex.submit(Function, ir, dtype=dt, ways=w) for dt in cand for w in cand[dt]}
+        fns = {k: f.result() for k, f in futs.items()}
 
     x_np = inputs.normal(64, N_INST, seed=INPUT_SEED + rank)
     x64 = torch.tensor(x_np, dtype=torch.float64, device=dev)
     x32 = x64.float()
-    y64 = torch.empty((fn64.nnz_out, N_INST), dtype=torch.float64, device=dev)
-    y32 = torch.empty((fn32.nnz_out, N_INST), dtype=torch.float32, device=dev)
+    y64 = torch.empty((32, N_INST), dtype=torch.float64, device=dev)
+    y32 = torch.empty((32, N_INST), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    tuning = {}
+    for dt, x, y in (("f64", x64, y64), ("f32", x32, y32)):
+        ms = {}
+        for w in cand[dt]:
+            fn = fns[(dt, w)]
+            for _ in range(2):
+                fn(x, out=y)
+            ts = []
+            for _ in range(3):
+                flush.zero_()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                fn(x, out=y)
+                e.record(stream)
+                e.synchronize()
+                ts.append(s.elapsed_time(e))
+            ms[w] = min(ts)
+        tuning[dt] = {"candidates_ms": {str(w): v for w, v in ms.items()}, "ways": min(ms, key=ms.get)}
+    fn64 = fns[("f64", tuning["f64"]["ways"])]
+    fn32 = fns[("f32", tuning["f32"]["ways"])]
 
     def timed(fn, x, y, steps):
         times = []
@@ -557,7 +586,12 @@ def main():
         "metric": METRIC, "value": value, "unit": "instance-evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(fn64.info),
+        "data": "synthetic",
+        "config": dict(workload_config(fn64.info), ways_f64=tuning["f64"]["ways"],
+                       ways_f32=tuning["f32"]["ways"],
+                       launch="ways = W: W warps share each group of 32 instances (cooperative "
+                              "kernel); ways = 0: one thread per instance"),
+        "ways_tuning_ms": tuning,
         "gop_per_s": ops_live * N_INST / t64 * 1e-9,
         "roofline": {"bound": "alu", "achieved": ach64 * 1e-12, "peak": pk64["fma_per_s"] * 1e-12,
                      "unit": "TFMA/s (FMA-equivalent ops, FP64)", "frac": ach64 / pk64["fma_per_s"],

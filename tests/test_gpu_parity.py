@@ -171,14 +171,17 @@ def test_strided_buffers_and_zero_batch():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("ways", [0, 2, 4])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_random_20k_program_full_batch_sampled(dtype):
-    """The 20,000-op workload at N = 65536 in the bench's launch configuration;
-    256 sampled instances (and the ragged tail) are checked against the oracle."""
+def test_random_20k_program_full_batch_sampled(dtype, ways):
+    """The 20,000-op workload at N = 65536 in each launch configuration the
+    bench chooses from (one thread per instance, or 2 or 4 warps per group of
+    32 instances); 256 sampled instances (and the ragged tail) are checked
+    against the oracle."""
     ir = programs.random_program(20000, seed=0).to_bytes()
     N = 65536
     x = inputs.normal(64, N, seed=1)
-    fn = Function(ir, dtype=dtype)
+    fn = Function(ir, dtype=dtype, ways=ways)
     if dtype == "f32":
         x = x.astype(np.float32).astype(np.float64)
     y = run(fn, x)
