@@ -37,7 +37,9 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from an ncu capture of the generated
 # kernel with this source hash (profiles/cs_fwd_f64_random20k.md); a kernel
 # whose source changed since gets no traffic figure
-NCU_TRAFFIC = {"c26c9219142915d9": 26148096 + 463616}
+NCU_TRAFFIC = {"c26c9219142915d9": 26148096 + 463616,   # one thread per instance
+               "95ad52848a2dde30": 26208000 + 11008,    # 2 warps per 32 instances
+               "562155cee3621147": 26315776 + 2560}     # 4 warps per 32 instances
 
 
 def workload_config(info=None):
