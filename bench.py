@@ -442,49 +442,27 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from concurrent.futures import ThreadPoolExecutor
-
     from paper_2408_09662_gb300 import inputs, peaks, programs
-    from paper_2408_09662_gb300.api import Function
+    from paper_2408_09662_gb300.api import tuned
 
     ir = programs.random_program(N_OPS_GEN, seed=PROGRAM_SEED).to_bytes()
-    # launch configuration: one thread per instance (ways 0) or W warps sharing each
-    # group of 32 instances (cooperative kernels); "auto" times the candidates once
-    # and keeps the fastest, as Batch.tune does for the tile size
-    cand = {"f64": [0, 2, 4] if args.ways64 == "auto" else [int(args.ways64)],
-            "f32": [0, 2, 4] if args.ways32 == "auto" else [int(args.ways32)]}
-    with ThreadPoolExecutor(6) as ex:   # the NVRTC compiles overlap (ctypes drops the GIL)
-        futs = {(dt, w): ex.submit(Function, ir, dtype=dt, ways=w) for dt in cand for w in cand[dt]}
-        fns = {k: f.result() for k, f in futs.items()}
-
     x_np = inputs.normal(64, N_INST, seed=INPUT_SEED + rank)
     x64 = torch.tensor(x_np, dtype=torch.float64, device=dev)
     x32 = x64.float()
-    y64 = torch.empty((32, N_INST), dtype=torch.float64, device=dev)
-    y32 = torch.empty((32, N_INST), dtype=torch.float32, device=dev)
+    # launch configuration: one thread per instance (ways 0) or W warps sharing each
+    # group of 32 instances (cooperative kernels); "auto" lets api.tuned time the
+    # candidates once and keep the fastest, as Batch.tune does for the tile size
+    cand = {"f64": (0, 2, 4) if args.ways64 == "auto" else (int(args.ways64),),
+            "f32": (0, 2, 4) if args.ways32 == "auto" else (int(args.ways32),)}
+    fn64 = tuned(ir, x64, "f64", cand["f64"])      # one after the other: the timings
+    fn32 = tuned(ir, x32, "f32", cand["f32"])      # must not share the GPU
+    tuning = {dt: {"candidates_ms": {str(w): v for w, v in fn.tuning_ms.items()}, "ways": fn.ways}
+              for dt, fn in (("f64", fn64), ("f32", fn32))}
+
+    y64 = torch.empty((fn64.nnz_out, N_INST), dtype=torch.float64, device=dev)
+    y32 = torch.empty((fn32.nnz_out, N_INST), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    tuning = {}
-    for dt, x, y in (("f64", x64, y64), ("f32", x32, y32)):
-        ms = {}
-        for w in cand[dt]:
-            fn = fns[(dt, w)]
-            for _ in range(2):
-                fn(x, out=y)
-            ts = []
-            for _ in range(3):
-                flush.zero_()
-                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s.record(stream)
-                fn(x, out=y)
-                e.record(stream)
-                e.synchronize()
-                ts.append(s.elapsed_time(e))
-            ms[w] = min(ts)
-        tuning[dt] = {"candidates_ms": {str(w): v for w, v in ms.items()}, "ways": min(ms, key=ms.get)}
-    fn64 = fns[("f64", tuning["f64"]["ways"])]
-    fn32 = fns[("f32", tuning["f32"]["ways"])]
 
     def timed(fn, x, y, steps):
         times = []

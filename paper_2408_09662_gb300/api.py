@@ -208,6 +208,40 @@ def apply(fn: Function, x: torch.Tensor) -> torch.Tensor:
     return _Apply.apply(fn, x)
 
 
+def tuned(program, x: torch.Tensor, dtype: str = "f64", candidates=(0, 2, 4), reps: int = 3,
+          flush_bytes: int = 256 << 20, **options) -> Function:
+    """The program compiled once per launch configuration in `candidates`
+    (ways: 0 = one thread per instance, W = W warps per group of 32
+    instances), the compiles running concurrently; each is timed on x (CUDA
+    events, L2 flushed before each launch, best of `reps`) and the fastest is
+    returned, with `.ways` and `.tuning_ms` recording the choice."""
+    from concurrent.futures import ThreadPoolExecutor
+    prog = _program_bytes(program)
+    with ThreadPoolExecutor(len(candidates)) as ex:   # ctypes drops the GIL while compiling
+        fns = dict(zip(candidates, ex.map(lambda w: Function(prog, dtype=dtype, ways=w, **options),
+                                          candidates)))
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device=x.device)
+    y = torch.empty((fns[candidates[0]].nnz_out, x.shape[1]), dtype=x.dtype, device=x.device)
+    ms = {}
+    for w, fn in fns.items():
+        for _ in range(2):
+            fn(x, out=y)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn(x, out=y)
+            e.record()
+            e.synchronize()
+            ts.append(s.elapsed_time(e))
+        ms[w] = min(ts)
+    best = min(ms, key=ms.get)
+    fn = fns[best]
+    fn.ways, fn.tuning_ms = best, ms
+    return fn
+
+
 class Batch:
     """Several programs, each over its own fixed instance count, evaluated by one
     persistent kernel replayed from a CUDA graph (mode "persistent") or by one

@@ -100,3 +100,15 @@ def test_cooperative_rollout_gradient_equals_plain():
     assert res[0][0] == res[1][0]
     for u, v in zip(res[0][1:], res[1][1:]):
         assert torch.equal(u, v)
+
+
+def test_tuned_picks_the_fastest_configuration_and_keeps_results():
+    from paper_2408_09662_gb300.api import tuned
+    ir = programs.cartpole_rk4().to_bytes()
+    x = torch.tensor(inputs.cartpole(4096, seed=70), device="cuda")
+    fn = tuned(ir, x, "f64", candidates=(0, 4), fmad=0)
+    assert fn.ways in (0, 4) and set(fn.tuning_ms) == {0, 4}
+    assert fn.tuning_ms[fn.ways] == min(fn.tuning_ms.values())
+    ref = Function(ir, dtype="f64", fmad=0)(x)
+    torch.cuda.synchronize()
+    assert torch.equal(fn(x), ref)
