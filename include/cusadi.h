@@ -8,7 +8,8 @@
  * instances on the GPU.  Only structural non-zeros of the sparse inputs and
  * outputs are read and written (§II-A).  Data stays on the GPU: every pointer
  * passed to the evaluation calls is a device pointer (§III intro: inputs and
- * outputs are stored only on the GPU).
+ * outputs are stored only on the GPU), except the host buffers of
+ * cusadi_eval_host, which copies them in and out itself.
  *
  * Layout of every batched buffer: instance-fastest ("SoA").  Row k of
  * instance i lives at  buf[k * ld + i]  with ld >= N (elements, not bytes).
@@ -24,7 +25,9 @@
  * Errors: every call returns a cusadi_status.  Argument errors are detected on
  * the host before anything is launched; cusadi_last_error() then returns a
  * message for the calling thread.  Evaluation calls are asynchronous on the
- * given stream; they never synchronise the host and never allocate memory.
+ * given stream.  The first call of a function on a device loads its kernels
+ * (allocates, synchronises); after that they neither synchronise the host nor
+ * allocate device memory.
  *
  * Threading: a cusadi_fn is immutable after cusadi_load and may be used from
  * several host threads and streams at once, provided the workspaces differ.
@@ -79,10 +82,11 @@ typedef struct {
   int32_t inline_math;        /* 1: inline transcendental functions (slow compile) (0) */
   int32_t adjoint;            /* 1: build the adjoint kernels at load; 0: at the first call
                                  that needs them (cusadi_adjoint and friends)   (0) */
-  int32_t ways;               /* >= 2: within-instance parallelism on the compiled forward
-                                 path: `ways` warps split each program across 32 instances
-                                 (latency-bound small batches, few-instance long programs);
-                                 0: one instance per thread                        (0) */
+  int32_t ways;               /* 2..16: within-instance parallelism on the compiled path
+                                 (forward and adjoint kernels): `ways` warps split each
+                                 program across a group of 32 instances (small batches,
+                                 few-instance long programs; at large batches it can also
+                                 win: time it); 0: one instance per thread          (0) */
   int32_t own_math;           /* 1: FP32 sin/cos/exp use the engine's own inline
                                  implementations (<= 2 ulp; measured slower than the
                                  library's on the random 20k-op program), 0: library (0) */
