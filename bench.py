@@ -415,7 +415,7 @@ def main():
     ap.add_argument("--ways64", default="auto",
                     help="warps per 32 instances of the FP64 kernel: auto (fastest of 0, 2, 4), or a number")
     ap.add_argument("--ways32", default="auto",
-                    help="warps per 32 instances of the FP32 kernel: auto (fastest of 0, 2, 4), or a number")
+                    help="warps per 32 instances of the FP32 kernel: auto (fastest of 0, 2, 4, 8), or a number")
     ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc"],
                     help="run one of the paper's experiments instead (markdown table, no JSON line); "
                          "ldlt adds the CPU oracle as its CPU baseline column")
@@ -453,7 +453,7 @@ def main():
     # group of 32 instances (cooperative kernels); "auto" lets api.tuned time the
     # candidates once and keep the fastest, as Batch.tune does for the tile size
     cand = {"f64": (0, 2, 4) if args.ways64 == "auto" else (int(args.ways64),),
-            "f32": (0, 2, 4) if args.ways32 == "auto" else (int(args.ways32),)}
+            "f32": (0, 2, 4, 8) if args.ways32 == "auto" else (int(args.ways32),)}
     fn64 = tuned(ir, x64, "f64", cand["f64"])      # one after the other: the timings
     fn32 = tuned(ir, x32, "f32", cand["f32"])      # must not share the GPU
     tuning = {dt: {"candidates_ms": {str(w): v for w, v in fn.tuning_ms.items()}, "ways": fn.ways}

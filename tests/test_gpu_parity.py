@@ -171,13 +171,13 @@ def test_strided_buffers_and_zero_batch():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("ways", [0, 2, 4])
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype,ways", [("f64", 0), ("f64", 2), ("f64", 4),
+                                        ("f32", 0), ("f32", 2), ("f32", 4), ("f32", 8)])
 def test_random_20k_program_full_batch_sampled(dtype, ways):
     """The 20,000-op workload at N = 65536 in each launch configuration the
-    bench chooses from (one thread per instance, or 2 or 4 warps per group of
-    32 instances); 256 sampled instances (and the ragged tail) are checked
-    against the oracle."""
+    bench chooses from (one thread per instance, or 2, 4 or (FP32) 8 warps per
+    group of 32 instances); 256 sampled instances (and the ragged tail) are
+    checked against the oracle."""
     ir = programs.random_program(20000, seed=0).to_bytes()
     N = 65536
     x = inputs.normal(64, N, seed=1)
