@@ -208,13 +208,13 @@ def apply(fn: Function, x: torch.Tensor) -> torch.Tensor:
     return _Apply.apply(fn, x)
 
 
-def tuned(program, x: torch.Tensor, dtype: str = "f64", candidates=(0, 2, 4), reps: int = 3,
+def tuned(program, x: torch.Tensor, dtype: str = "f64", candidates=(0, 2, 4), reps: int = 5,
           flush_bytes: int = 256 << 20, **options) -> Function:
     """The program compiled once per launch configuration in `candidates`
     (ways: 0 = one thread per instance, W = W warps per group of 32
     instances), the compiles running concurrently; each is timed on x (CUDA
-    events, L2 flushed before each launch, best of `reps`) and the fastest is
-    returned, with `.ways` and `.tuning_ms` recording the choice."""
+    events, L2 flushed before each launch, median of `reps`) and the fastest
+    is returned, with `.ways` and `.tuning_ms` recording the choice."""
     from concurrent.futures import ThreadPoolExecutor
     prog = _program_bytes(program)
     with ThreadPoolExecutor(len(candidates)) as ex:   # ctypes drops the GIL while compiling
@@ -235,7 +235,7 @@ def tuned(program, x: torch.Tensor, dtype: str = "f64", candidates=(0, 2, 4), re
             e.record()
             e.synchronize()
             ts.append(s.elapsed_time(e))
-        ms[w] = min(ts)
+        ms[w] = sorted(ts)[len(ts) // 2]
     best = min(ms, key=ms.get)
     fn = fns[best]
     fn.ways, fn.tuning_ms = best, ms
