@@ -383,6 +383,8 @@ def run_experiment(name):
         experiments.coop_sweep()
     elif name == "mpc":
         experiments.mpc_pareto()
+    elif name == "roa":
+        experiments.lqr_roa()
     else:
         from oracle import Oracle
         cores = os.cpu_count() or 1
@@ -416,7 +418,7 @@ def main():
                     help="warps per 32 instances of the FP64 kernel: auto (faster of 0, 4), or a number")
     ap.add_argument("--ways32", default="auto",
                     help="warps per 32 instances of the FP32 kernel: auto (fastest of 0, 2, 4, 8), or a number")
-    ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc"],
+    ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc", "roa"],
                     help="run one of the paper's experiments instead (markdown table, no JSON line); "
                          "ldlt adds the CPU oracle as its CPU baseline column")
     args = ap.parse_args()

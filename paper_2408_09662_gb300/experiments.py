@@ -3,6 +3,7 @@ markdown table.
 
     python -m paper_2408_09662_gb300.experiments ldlt   # §IV benchmark family, batch-size sweep
     python -m paper_2408_09662_gb300.experiments coop   # within-instance parallelism (§VI)
+    python -m paper_2408_09662_gb300.experiments roa    # LQR quadcopter region of attraction (§V-C)
     python -m paper_2408_09662_gb300.experiments mpc    # MPC cost/violation vs iterations (§V-A, Fig. 4)
     python -m paper_2408_09662_gb300.experiments one random20k f64 4096 8   # one kernel, for a profiler
     python -m paper_2408_09662_gb300.experiments one srb f64 65536 0 adjoint
@@ -203,6 +204,47 @@ def mpc_pareto(N=4096, steps=100, Ms=(1, 2, 3, 5, 8), warm_Ms=(1, 2), dtype="f64
     return rows
 
 
+def lqr_roa(N=10000, steps=250, u_maxes=(6.0, 8.0, 10.0, 15.0, 20.0), seed=3, dtype="f64"):
+    """Region of attraction of the LQR-controlled planar quadcopter (§V-C):
+    N closed loops from zero position and angle with initial velocities
+    (v_x, v_z) ~ U(-3, 3)^2 and angular rate ~ U(-24, 24), for each thrust
+    limit; each step evaluates quadrotor_lqr_step (SDA Riccati solve inside)
+    for all instances.  A run is stable if |z| < 0.5 everywhere after `steps`
+    steps.  Prints the stable fraction per thrust limit and initial-speed bin,
+    and the time per closed-loop step."""
+    fn = Function(programs.quadrotor_lqr_step().to_bytes(), dtype=dtype)
+    rng = np.random.default_rng(seed)
+    v0 = np.vstack([rng.uniform(-3, 3, (2, N)), rng.uniform(-24, 24, (1, N))])
+    speed = np.sqrt(v0[0] ** 2 + v0[1] ** 2)
+    bins = [0.0, 1.0, 2.0, 3.0, 5.0]
+    print(f"| thrust limit | stable (all) | " + " | ".join(f"|v| in [{a:g}, {b:g})" for a, b in zip(bins, bins[1:]))
+          + f" | ms per step (N = {N}) |")
+    print("|---|---|" + "---|" * (len(bins) - 1) + "---|")
+    rows = []
+    for u_max in u_maxes:
+        X = np.zeros((16, N))
+        X[3:6] = v0
+        X[6], X[7], X[8], X[9:15], X[15] = u_max, 1.0, 0.01, 5.0, 0.1
+        buf = [torch.tensor(X, dtype=fn.torch_dtype, device="cuda") for _ in range(2)]
+        fn(buf[0], out=buf[1][:6])
+        torch.cuda.synchronize()
+        buf[0].copy_(torch.tensor(X, dtype=fn.torch_dtype, device="cuda"))
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for t in range(steps):
+            fn(buf[t % 2], out=buf[(t + 1) % 2][:6])
+        e.record()
+        e.synchronize()
+        z = buf[steps % 2][:6].double().cpu().numpy()
+        stable = np.all(np.abs(z) < 0.5, axis=0) & np.all(np.isfinite(z), axis=0)
+        frac = [float(stable[(speed >= a) & (speed < b)].mean()) for a, b in zip(bins, bins[1:])]
+        ms = s.elapsed_time(e) / steps
+        rows.append((u_max, float(stable.mean()), frac, ms))
+        print(f"| {u_max:g} | {stable.mean():.3f} | " + " | ".join(f"{f:.3f}" for f in frac) + f" | {ms:.3f} |",
+              flush=True)
+    return rows
+
+
 def one_kernel(program="random20k", dtype="f64", N=4096, ways=0, reps=3, adjoint=False):
     """Compile one program and launch it `reps` times (a small case for a
     profiler); adjoint: its reverse sweep (broadcast rows reduced) instead."""
@@ -233,6 +275,8 @@ def main(argv):
         coop_sweep()
     elif which == "mpc":
         mpc_pareto()
+    elif which == "roa":
+        lqr_roa()
     elif which == "one":
         # one <program> <dtype> <N> <ways> [adjoint]
         prog, dt, N, w = (argv[2:] + ["random20k", "f64", "4096", "0"][len(argv) - 2:])[:4]
