@@ -90,6 +90,9 @@ typedef struct {
   int32_t own_math;           /* 1: FP32 sin/cos/exp use the engine's own inline
                                  implementations (<= 2 ulp; measured slower than the
                                  library's on the random 20k-op program), 0: library (0) */
+  int32_t debug_checks;       /* 1: compiled kernels count every non-finite value they
+                                 store (NaN, +-inf) in a device counter that
+                                 cusadi_debug_count reads; 0: no checks            (0) */
   const char* cache_dir;      /* directory for compiled kernels, NULL = in-memory only */
 } cusadi_options;
 
@@ -238,6 +241,16 @@ cusadi_status cusadi_eval_noalloc(cusadi_fn fn, const void* in, int64_t ld_in, v
 cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in, void* out_host,
                                int64_t ld_out, int64_t N, void* dev_in, void* dev_out,
                                void* workspace, int32_t chunks, cusadi_stream stream);
+
+/* Debug: the number of non-finite values (NaN, +-inf) the function's kernels
+ * stored on the current device since the previous call, and the counter reset
+ * to 0.  Needs a function loaded with debug_checks = 1 on the compiled path
+ * (INVALID_ARG otherwise, checked before any CUDA call; UNSUPPORTED on the
+ * interpreter path).  Synchronises the device (a debugging call, not for the
+ * hot loop).  Kernels count values that they write to outputs (and, for an
+ * adjoint, to the reduction workspace); a function never evaluated on the
+ * device reads 0. */
+cusadi_status cusadi_debug_count(cusadi_fn fn, uint64_t* count);
 
 /* Output argument `arg` as a dense matrix per instance.  The engine reads and
  * writes only structural non-zeros (§II-A: sparse CasADi matrices, Listing 2

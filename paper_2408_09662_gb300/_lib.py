@@ -38,6 +38,7 @@ class cusadi_options(ctypes.Structure):
                 ("segment_ops", c_int64), ("block", c_int32), ("maxrregcount", c_int32),
                 ("fmad", c_int32), ("compile_threads", c_int32), ("schedule", c_int32),
                 ("inline_math", c_int32), ("adjoint", c_int32), ("ways", c_int32), ("own_math", c_int32),
+                ("debug_checks", c_int32),
                 ("cache_dir", c_char_p)]
 
 
@@ -76,6 +77,7 @@ SIGNATURES = {
     "cusadi_adjoint": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                  c_int64, c_uint32, c_void_p, c_void_p]),
     "cusadi_eval_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p]),
+    "cusadi_debug_count": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "cusadi_densify": (c_int32, [c_void_p, ctypes.c_int, c_void_p, c_int64, c_void_p, c_int64, c_int64,
                                  c_void_p]),
     "cusadi_eval_host": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p,
@@ -184,6 +186,12 @@ def cusadi_eval_host(fn: int, in_host: int, ld_in: int, out_host: int, ld_out: i
                      dev_in: int, dev_out: int, workspace: int, chunks: int, stream: int) -> None:
     check(lib().cusadi_eval_host(fn, in_host, ld_in, out_host, ld_out, N, dev_in, dev_out,
                                  workspace, chunks, stream), "cusadi_eval_host")
+
+
+def cusadi_debug_count(fn: int) -> int:
+    n = ctypes.c_uint64(0)
+    check(lib().cusadi_debug_count(fn, ctypes.byref(n)), "cusadi_debug_count")
+    return int(n.value)
 
 
 def cusadi_densify(fn: int, arg: int, y: int, ld_y: int, dense: int, ld_d: int, N: int,

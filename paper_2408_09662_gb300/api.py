@@ -117,6 +117,10 @@ class Function:
                       torch.cuda.current_stream(x.device).cuda_stream)
         return out
 
+    def debug_count(self) -> int:
+        """Non-finite values stored since the last call (needs debug_checks=1)."""
+        return L.cusadi_debug_count(self._fn)
+
     def dense(self, y: torch.Tensor, arg: int) -> torch.Tensor:
         """Output argument `arg` of a result y [nnz_out, N] as a dense
         [nrow, ncol, N] tensor (structural zeros filled in on the GPU)."""

@@ -311,6 +311,8 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
       } else {
         body << "  Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
       }
+      if (o.debug_checks && !o.device_fn)   // count non-finite results (cusadi_debug_count)
+        body << "  if (active && !isfinite((double)(" << v << "))) atomicAdd(&cs_dbg, 1u);\n";
     };
     // outputs fed directly by inputs or constants are written by segment 0
     if (s == 0) {
@@ -339,6 +341,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
         << (o.adjoint ? " (adjoint)" : "") << ", dtype "
         << (o.dtype == CUSADI_F64 ? "f64" : (o.dtype == CUSADI_F32 ? "f32" : "mixed")) << "\n";
     if (G.own_f32) src << kOwnMathF32;
+    if (o.debug_checks && !o.device_fn) src << "__device__ unsigned int cs_dbg;   // non-finite results\n";
     if (!o.inline_math) {
       for (auto& c : G.calls) {
         MathFn m = math_name(c.first);
@@ -538,6 +541,8 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
       R.reduce_rows.push_back((int64_t)r);
     }
   auto store_out = [&](std::ostringstream& body, int64_t r, const std::string& v) {
+    if (o.debug_checks && !o.device_fn)   // count non-finite results (cusadi_debug_count)
+      body << "    if (active && !isfinite((double)(" << v << "))) atomicAdd(&cs_dbg, 1u);\n";
     if (!o.adjoint) {
       body << "    if (active) Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
       return;
@@ -664,6 +669,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     src << "// Generated cooperative kernel: segment " << s << " of " << nseg << ", " << W
         << " warps per 32 instances, " << (segs[s].second - segs[s].first) << " phases\n";
     if (G.own_f32) src << kOwnMathF32;
+    if (o.debug_checks && !o.device_fn) src << "__device__ unsigned int cs_dbg;   // non-finite results\n";
     if (!o.inline_math) {
       for (auto& c : G.calls) {
         MathFn m = math_name(c.first);

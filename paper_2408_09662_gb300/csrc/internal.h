@@ -112,6 +112,7 @@ struct CodegenOptions {
   bool device_fn = false;        // emit relocatable __device__ functions of one instance
                                  // (cooperative: of one group of 32, called by the whole CTA)
   int coop_shared_kb = 160;      // shared memory for cross-warp values (cooperative)
+  bool debug_checks = false;     // count non-finite stored values in the module's cs_dbg
   std::string prefix = "cs_fwd";
 };
 
@@ -185,6 +186,7 @@ struct Driver {
   CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
   CUresult (*funcGetAttribute)(int*, CUfunction_attribute, CUfunction) = nullptr;
   CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+  CUresult (*moduleGetGlobal)(CUdeviceptr*, size_t*, CUmodule, const char*) = nullptr;
   bool ok = false;
 };
 const Driver& driver();

@@ -135,7 +135,8 @@ const Driver& driver() {
            get("cuLaunchKernel", (void**)&d.launchKernel) &&
            get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&d.occupancy) &&
            get("cuFuncGetAttribute", (void**)&d.funcGetAttribute) &&
-           get("cuFuncSetAttribute", (void**)&d.funcSetAttribute);
+           get("cuFuncSetAttribute", (void**)&d.funcSetAttribute) &&
+           get("cuModuleGetGlobal", (void**)&d.moduleGetGlobal);
   });
   return d;
 }
@@ -217,6 +218,7 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.segment_ops = fn->opt.segment_ops;
   co.inline_math = fn->opt.inline_math != 0;
   co.own_math = fn->opt.own_math != 0;
+  co.debug_checks = fn->opt.debug_checks != 0;
   co.adjoint = adjoint;
   co.split = adjoint ? fn->ir.nnz_in : -1;
   static const char* tag[] = {"f64", "f32", "mixed"};
@@ -494,6 +496,7 @@ void cusadi_default_options(cusadi_options* o) {
   o->adjoint = 0;
   o->own_math = 0;
   o->ways = 0;
+  o->debug_checks = 0;
   o->cache_dir = nullptr;
 }
 
@@ -669,6 +672,32 @@ cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out
   cusadi_status s = device_state(fn, false, &ds);
   if (s != CUSADI_OK) return s;
   return run(fn, fn->fwd, *ds, false, in, ld_in, nullptr, 0, out, ld_out, N, workspace, 0, 0, stream);
+}
+
+cusadi_status cusadi_debug_count(cusadi_fn fn, uint64_t* count) {
+  if (!fn || !count) return fail(CUSADI_E_INVALID_ARG, "NULL argument");
+  *count = 0;
+  if (!fn->opt.debug_checks) return fail(CUSADI_E_INVALID_ARG, "function loaded without debug_checks");
+  if (fn->path == CUSADI_PATH_INTERP)
+    return fail(CUSADI_E_UNSUPPORTED, "debug checks exist on the compiled path only");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return cuda_fail("cudaGetDevice", ce);
+  std::lock_guard<std::mutex> lk(fn->dev_mu);
+  auto it = fn->dev.find(dev);
+  if (it == fn->dev.end()) return CUSADI_OK;          // never evaluated here
+  if ((ce = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail("cudaDeviceSynchronize", ce);
+  for (CUmodule m : it->second.mods) {
+    CUdeviceptr p = 0;
+    size_t bytes = 0;
+    if (driver().moduleGetGlobal(&p, &bytes, m, "cs_dbg") != CUDA_SUCCESS || bytes != sizeof(unsigned)) continue;
+    unsigned v = 0;
+    if ((ce = cudaMemcpy(&v, (const void*)p, sizeof v, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail("cudaMemcpy", ce);
+    if ((ce = cudaMemset((void*)p, 0, sizeof v)) != cudaSuccess) return cuda_fail("cudaMemset", ce);
+    *count += v;
+  }
+  return CUSADI_OK;
 }
 
 cusadi_status cusadi_densify(cusadi_fn fn, int arg, const void* y, int64_t ld_y, void* dense,

@@ -340,3 +340,27 @@ def test_concurrent_calls_on_different_streams():
         cur.wait_stream(st)
     torch.cuda.synchronize()
     assert torch.equal(y, ref)
+
+
+@pytest.mark.parametrize("ways", [0, 4])
+def test_debug_checks_count_non_finite_results(ways):
+    """debug_checks=1: log and sqrt of negative inputs give NaN; the kernels
+    count every non-finite value they store, cusadi_debug_count reads and
+    resets the counter, and finite results count nothing."""
+    from paper_2408_09662_gb300 import tracer as T
+    g = T.Graph()
+    x = g.symbols(2)
+    ir = T.Function([("x", x)], [("y", [T.log(x[0]), T.sqrt(x[1]), x[0] * x[1]])]).to_ir().to_bytes()
+    fn = Function(ir, dtype="f64", debug_checks=1, ways=ways)
+    N = 5000
+    X = np.ones((2, N))
+    X[0, :37] = -1.0                       # log(-1) = NaN
+    X[1, 100:112] = -4.0                   # sqrt(-4) = NaN
+    X[0, 200] = 0.0                        # log(0) = -inf
+    x_d = torch.tensor(X, device="cuda")
+    y = fn(x_d)
+    assert fn.debug_count() == 37 + 12 + 1
+    assert fn.debug_count() == 0           # read and reset
+    fn(torch.ones((2, N), dtype=torch.float64, device="cuda"), out=y)
+    assert fn.debug_count() == 0
+    assert np.isnan(y.cpu().numpy()[0, :37]).all()

@@ -33,6 +33,30 @@ def test_library_exports_every_declared_entry_point():
 def test_default_options():
     o = L.cusadi_default_options()
     assert (o.dtype, o.path, o.block, o.fmad, o.schedule) == (0, 0, 128, 1, 1)
+    assert (o.ways, o.own_math, o.debug_checks, o.adjoint) == (0, 0, 0, 0)
+
+
+def test_debug_checks_instrument_the_stores():
+    ir = programs.cartpole_rk4().to_bytes()
+    plain = L.cusadi_load(ir, _opt())
+    dbg = L.cusadi_load(ir, _opt(debug_checks=1))
+    coop = L.cusadi_load(ir, _opt(debug_checks=1, ways=4))
+    interp = L.cusadi_load(ir, _opt(debug_checks=1, path=L.CUSADI_PATH_INTERP))
+    try:
+        assert "cs_dbg" not in L.cusadi_source(plain)
+        for fn in (dbg, coop):
+            src = L.cusadi_source(fn)
+            assert "__device__ unsigned int cs_dbg;" in src
+            assert src.count("atomicAdd(&cs_dbg, 1u)") == 24          # one per output row
+        with pytest.raises(L.CusadiError) as e:
+            L.cusadi_debug_count(plain)                               # no checks compiled in
+        assert e.value.status == L.CUSADI_E_INVALID_ARG
+        with pytest.raises(L.CusadiError) as e:
+            L.cusadi_debug_count(interp)
+        assert e.value.status == L.CUSADI_E_UNSUPPORTED
+    finally:
+        for fn in (plain, dbg, coop, interp):
+            L.cusadi_free(fn)
 
 
 def _opt(**kw):
