@@ -360,7 +360,7 @@ def test_debug_checks_count_non_finite_results(ways):
     x_d = torch.tensor(X, device="cuda")
     y = fn(x_d)
     assert fn.debug_count() == 37 + 12 + 1
+    assert np.isnan(y.cpu().numpy()[0, :37]).all()
     assert fn.debug_count() == 0           # read and reset
     fn(torch.ones((2, N), dtype=torch.float64, device="cuda"), out=y)
     assert fn.debug_count() == 0
-    assert np.isnan(y.cpu().numpy()[0, :37]).all()
