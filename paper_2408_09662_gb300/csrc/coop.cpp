@@ -165,7 +165,7 @@ CoopPlan plan_eft(const Graph& g, int ways, double comm_cost) {
     if (leaf(i)) continue;
     const Node& x = g.nodes[i];
     int best = 0;
-    double best_f = 1e300, best_start = 0;
+    double best_f = 1e300;
     for (int w = 0; w < ways; ++w) {
       double start = avail[w];
       for (int32_t o : {x.a, x.b})
@@ -174,10 +174,8 @@ CoopPlan plan_eft(const Graph& g, int ways, double comm_cost) {
       if (f < best_f - 1e-12 || (f < best_f + 1e-12 && avail[w] < avail[best])) {
         best = w;
         best_f = f;
-        best_start = start;
       }
     }
-    (void)best_start;
     P.owner[i] = best;
     finish[i] = best_f;
     avail[best] = best_f;
