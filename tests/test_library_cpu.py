@@ -300,15 +300,19 @@ def test_injected_compile_failure_falls_back_to_the_interpreter_under_auto():
     assert out == [str(L.CUSADI_PATH_INTERP), str(L.CUSADI_E_COMPILE)]
 
 
+@pytest.mark.parametrize("shared_kb", [None, "1"])
 @pytest.mark.parametrize("ways", [2, 4, 8, 16])
-def test_cooperative_kernels_reach_every_barrier(ways):
+def test_cooperative_kernels_reach_every_barrier(ways, shared_kb, monkeypatch):
     """Cooperative kernels are laid out phase by phase: each phase holds one
     `if (warp == w)` block per warp with work, and the phases are separated by
     __syncthreads() at function scope, so every thread of the CTA executes the
     same barrier instructions.  Simulating the phases, every value a warp reads
     from shared memory or the workspace was written by its owner in an earlier
-    phase and not overwritten before the read."""
+    phase and not overwritten before the read.  With a 1 KB shared budget
+    nearly every cross-warp value goes through workspace rows instead."""
     import re as _re
+    if shared_kb is not None:
+        monkeypatch.setenv("CUSADI_COOP_SHARED_KB", shared_kb)
 
     def sources(fn):
         for adjoint in (False, True):      # the adjoint kernels are cooperative too
@@ -337,9 +341,15 @@ def test_cooperative_kernels_reach_every_barrier(ways):
                             writes.setdefault(("s", m.group(1)), []).append((ph, int(w), m.group(2)))
                         for m in _re.finditer(r"v(\d+)_\d+ = \(\w+\)cs_x\[(\d+) \* 32 \+ lane\];", block):
                             reads.append((ph, int(w), ("s", m.group(2)), m.group(1)))
+                        for m in _re.finditer(r"if \(active\) W\[(\d+)ll \* ldw\] = \(\w+\)v(\d+);", block):
+                            writes.setdefault(("g", m.group(1)), []).append((ph, int(w), m.group(2)))
+                        for m in _re.finditer(r"v(\d+)_\d+ = \(\w+\)W\[(\d+)ll \* ldw\];", block):
+                            reads.append((ph, int(w), ("g", m.group(2)), m.group(1)))
                 for ph, w, loc, var in reads:
                     ws = writes.get(loc, [])
                     mine = [x for x in ws if x[2] == var]
+                    if loc[0] == "g" and not mine:
+                        continue          # a row carried from an earlier kernel of the program
                     assert mine and mine[0][0] < ph and mine[0][1] != w
                     assert not [x for x in ws if x[2] != var and mine[0][0] <= x[0] <= ph]
         finally:
