@@ -364,3 +364,34 @@ def test_debug_checks_count_non_finite_results(ways):
     assert fn.debug_count() == 0           # read and reset
     fn(torch.ones((2, N), dtype=torch.float64, device="cuda"), out=y)
     assert fn.debug_count() == 0
+
+
+@pytest.mark.parametrize("path,ways", [("compiled", 0), ("interp", 0), ("compiled", 2)])
+def test_degenerate_programs(path, ways):
+    """Outputs that are a constant, a copy of an input and a product; one
+    instance and a ragged batch; a program whose inputs are all broadcast,
+    read from a one-column buffer (ld_in = 1), gives the same value everywhere."""
+    from paper_2408_09662_gb300 import tracer as T
+    from paper_2408_09662_gb300.ir import ARG_BROADCAST
+    g = T.Graph()
+    x = g.symbols(2)
+    ir = T.Function([("x", x)], [("y", [2.5, x[1], x[0] * x[1]])]).to_ir().to_bytes()
+    fn = Function(ir, dtype="f64", path=path, ways=ways)
+    for N in (1, 37):
+        X = np.random.default_rng(N).standard_normal((2, N))
+        y = fn(torch.tensor(X, device="cuda")).cpu().numpy()
+        np.testing.assert_array_equal(y[0], np.full(N, 2.5))
+        np.testing.assert_array_equal(y[1], X[1])
+        np.testing.assert_array_equal(y[2], X[0] * X[1])
+    g = T.Graph()
+    k = g.symbols(2)
+    irb = T.Function([("k", k, ARG_BROADCAST)], [("y", [T.sin(k[0]) * k[1]])]).to_ir().to_bytes()
+    fb = Function(irb, dtype="f64", path=path, ways=ways)
+    kk = torch.tensor([[0.5], [3.0]], dtype=torch.float64, device="cuda")        # [2, 1]
+    out = torch.empty((1, 100), dtype=torch.float64, device="cuda")
+    from paper_2408_09662_gb300 import _lib as L
+    L.cusadi_eval(fb._fn, kk.data_ptr(), 1, out.data_ptr(), 100, 100,
+                  0, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert np.allclose(out.cpu().numpy(), np.sin(0.5) * 3.0, rtol=1e-15, atol=0)
+    assert len(set(out.cpu().numpy().ravel().tolist())) == 1

@@ -172,6 +172,7 @@ def test_eval_host_argument_errors_are_caught_on_the_host():
     fn = L.cusadi_load(programs.listing2().to_bytes(), _opt())
     try:
         L.cusadi_eval_host(fn, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)             # N = 0 is a no-op
+        L.cusadi_densify(fn, 0, 0, 0, 0, 0, 0, 0)                           # likewise
         bad = [(fn, 8, 16, 8, 16, -1, 8, 8, 0, 0, 0),                    # N < 0
                (fn, 0, 16, 8, 16, 16, 8, 8, 0, 0, 0),                    # NULL host input
                (fn, 8, 16, 8, 16, 16, 0, 8, 0, 0, 0),                    # NULL device input
