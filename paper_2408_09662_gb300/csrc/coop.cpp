@@ -15,6 +15,7 @@
 //    level), so every warp carries about the same work between barriers.
 //    Several targets are tried.
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <queue>
 
@@ -36,7 +37,15 @@ double op_cost(int op) {
   }
 }
 
-constexpr double kBarrierCost = 6.0;   // a CTA barrier plus the shared-memory hand-off, in op costs
+// a CTA barrier plus the shared-memory hand-off, in op costs (CUSADI_COOP_BARRIER_COST
+// overrides it, for sweeps of the phase count against compile time and run time)
+double barrier_cost() {
+  static const double c = [] {
+    const char* e = std::getenv("CUSADI_COOP_BARRIER_COST");
+    return e ? std::max(0.0, std::atof(e)) : 6.0;
+  }();
+  return c;
+}
 
 bool is_leaf(const Graph& g, int64_t i) { return g.nodes[i].op == INPUT || g.nodes[i].op == CONST; }
 
@@ -48,7 +57,7 @@ double estimate(const Graph& g, const CoopPlan& P) {
   double t = 0;
   for (int q = 0; q < P.n_phases; ++q)
     t += *std::max_element(load.begin() + (size_t)q * P.ways, load.begin() + (size_t)(q + 1) * P.ways) +
-         kBarrierCost;
+         barrier_cost();
   return t;
 }
 
