@@ -325,3 +325,106 @@ def test_oracle_rejects_malformed_programs():
         Oracle(bad.to_bytes())
     with pytest.raises(OracleError):
         Oracle(good.to_bytes()[:40])           # truncated
+
+
+# ---------------------------------------------------------------------------
+# rounding bound: tight on programs whose first-order bound has a closed form,
+# and not far above the error actually observed against mpmath
+# ---------------------------------------------------------------------------
+_U53, _U24 = np.ldexp(1.0, -53), np.ldexp(1.0, -24)
+
+
+def _chain(op: Op, k: int) -> bytes:
+    """s_1 = x_1, s_j = s_{j-1} (op) x_j for j = 2..k; one output s_k."""
+    ins = [Instr(Op.INPUT, j, j) for j in range(k)]
+    ins.append(Instr(op, k, 0, 1))
+    for j in range(2, k):
+        ins.append(Instr(op, k, k, j))
+    ins.append(Instr(Op.OUTPUT, 0, k))
+    return ProgramIR(k + 1, [Sparsity.dense(k, 1, "x")], [Sparsity.dense(1, 1, "s")], ins, []).to_bytes()
+
+
+def test_rounding_bound_of_recursive_summation_is_the_closed_form():
+    """Recursive summation of positive terms: to first order the computed sum's
+    error is bounded by u * (sum of the partial sums s_2..s_k) (Higham, Accuracy
+    and Stability of Numerical Algorithms, §4.2), plus u * sum x_j when every
+    term is first rounded to float.  The FP64 bound covers two evaluations
+    (GPU and oracle), hence 2u per addition."""
+    k, N = 40, 64
+    x = inputs.uniform(k, N, 0.5, 2.0, seed=41)
+    orc = Oracle(_chain(Op.ADD, k))
+    partial = np.cumsum(x, axis=0)            # same left-to-right order as the chain
+    ref0 = 2 * _U53 * partial[1:].sum(axis=0)
+    ref1 = _U24 * x.sum(axis=0) + _U24 * partial[1:].sum(axis=0)
+    np.testing.assert_allclose(orc.rounding_bound(x, kind=0)[0], ref0, rtol=1e-12)
+    np.testing.assert_allclose(orc.rounding_bound(x, kind=1)[0], ref1, rtol=1e-12)
+
+
+def test_rounding_bound_of_a_product_chain_is_the_closed_form():
+    """A product of k factors carries k-1 roundings, each of relative size at
+    most u, so the first-order bound is (k-1) u |p| (Higham §3.1, Lemma 3.1);
+    rounding the k factors to float adds k u |p|."""
+    k, N = 30, 64
+    x = inputs.uniform(k, N, -1.5, 1.5, seed=42)
+    orc = Oracle(_chain(Op.MUL, k))
+    p = np.abs(orc.eval(x)[0])
+    np.testing.assert_allclose(orc.rounding_bound(x, kind=0)[0], 2 * _U53 * (k - 1) * p, rtol=1e-12)
+    np.testing.assert_allclose(orc.rounding_bound(x, kind=1)[0], _U24 * (2 * k - 1) * p, rtol=1e-12)
+
+
+def test_rounding_bound_is_not_inflated_on_random_programs():
+    """The first-order bound must hold (checked above) but not be loose by orders
+    of magnitude: per output, the largest bound over instances stays within a
+    fixed factor of the largest error observed against 40-digit truth.  The
+    factor 300 sits about 4x above what this seeded program shows, so a bound
+    inflated 10x fails."""
+    ir = programs.random_program(3000, seed=11).to_bytes()
+    orc = Oracle(ir)
+    x = inputs.normal(64, 16, seed=1)
+    exact = np.array([[float(v) for v in row] for row in mp_eval(ir, x.tolist(), dps=40)])
+    for mode, kind in ((MODE_F64, 0), (MODE_F32, 1)):
+        err = np.abs(orc.eval(x, mode=mode) - exact).max(axis=1)
+        B = orc.rounding_bound(x, kind=kind).max(axis=1)
+        assert np.all(B >= err)
+        ratio = float(np.median(B / np.maximum(err, 1e-300)))
+        assert 2.0 <= ratio <= 300.0, (kind, ratio)
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP64-tagged instructions keep doubles, the rest are float
+# ---------------------------------------------------------------------------
+def test_mixed_emulation_is_bit_exact_step_by_step():
+    """A program mixing tagged and untagged instructions, evaluated by hand in
+    numpy float32/float64 one instruction at a time.  Untagged instructions round
+    their operands and result to float; tagged ones take their operands as stored
+    and keep a double result; outputs land in a float buffer."""
+    from oracle import MODE_MIXED
+    from paper_2408_09662_gb300.ir import FLAG_F64
+    ins = [Instr(Op.INPUT, 0, 0), Instr(Op.INPUT, 1, 1), Instr(Op.INPUT, 2, 2),
+           Instr(Op.MUL, 3, 0, 1),                           # float
+           Instr(Op.CONST, 4, 0, flags=FLAG_F64),             # 0.1 as a double
+           Instr(Op.DIV, 5, 3, 4, flags=FLAG_F64),            # double / double
+           Instr(Op.SQRT, 6, 5, flags=FLAG_F64),              # double
+           Instr(Op.ADD, 7, 6, 2),                            # float(t6) + float(x2)
+           Instr(Op.CONST, 8, 0),                             # 0.1 as a float
+           Instr(Op.MUL, 7, 7, 8),                            # float
+           Instr(Op.MUL, 9, 7, 5, flags=FLAG_F64),            # float value times double
+           Instr(Op.OUTPUT, 0, 5), Instr(Op.OUTPUT, 1, 9), Instr(Op.OUTPUT, 2, 7)]
+    ir = ProgramIR(10, [Sparsity.dense(3, 1, "x")], [Sparsity.dense(3, 1, "y")], ins, [0.1]).to_bytes()
+    x = inputs.uniform(3, 4096, 0.5, 2.0, seed=43)
+    orc = Oracle(ir)
+    y = orc.eval(x, mode=MODE_MIXED)
+
+    x32 = x.astype(np.float32)
+    t3 = x32[0] * x32[1]
+    t5 = t3.astype(np.float64) / np.float64(0.1)
+    t6 = np.sqrt(t5)
+    t7 = (t6.astype(np.float32) + x32[2]) * np.float32(0.1)
+    t9 = t7.astype(np.float64) * t5
+    assert t3.dtype == t7.dtype == np.float32 and t5.dtype == t9.dtype == np.float64
+    ref = np.stack([t5.astype(np.float32), t9.astype(np.float32), t7]).astype(np.float64)
+    np.testing.assert_array_equal(y, ref)
+    # the step-by-step evaluation separates the modes: ignoring the tags, or
+    # tagging everything, changes the bits
+    assert np.any(orc.eval(x, mode=MODE_F32) != y)
+    assert np.any(orc.eval(x, mode=MODE_F64).astype(np.float32).astype(np.float64) != y)
