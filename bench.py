@@ -150,7 +150,39 @@ def _events_ms(fn, reps, flush):
     return statistics.median(ts)
 
 
-def other_configs(dev, pk64, pk32, flush, reps):
+def batch_oracle_check(irs, sizes, xs, outs, sample=64):
+    """CPU-baseline leg of the uneven batch: the FP64 oracle on `sample` sampled
+    instances (plus the last one) of every program, all host cores; its outputs
+    double as the per-output error record of the FP32 batch."""
+    from oracle import Oracle, tolerance
+    cores = os.cpu_count() or 1
+    per, op_inst, t_cpu = [], 0, 0.0
+    for j, (n, N) in enumerate(sizes):
+        idx = np.unique(np.r_[np.random.default_rng(j).choice(N, sample, replace=False), N - 1])
+        x = xs[j][:, idx].double().cpu().numpy()
+        got = outs[j][:, idx].double().cpu().numpy()
+        orc = Oracle(irs[j])
+        t0 = time.perf_counter()
+        ref = orc.eval(x, threads=cores)
+        t_cpu += time.perf_counter() - t0
+        op_inst += n * len(idx)
+        s = np.max(np.abs(ref), axis=1, keepdims=True)
+        rel = np.abs(got - ref) / s
+        tol = tolerance(orc, x, ref, 2e-4, kind=1, mca_runs=8)
+        per.append({"ops_generated": n, "instances_checked": int(len(idx)),
+                    "max_rel_scaled": float(rel.max()), "median_rel_scaled": float(np.median(rel)),
+                    "frac_within_2e-4": float(np.mean(rel <= 2e-4)),
+                    "frac_within_rule": float(np.mean(np.abs(got - ref) <= tol))})
+    return {"rule": "per output row k: |y32 - y64_oracle| <= max(2e-4 s_k, 2 B32, 4 S_k); B32 the "
+                    "first-order rounding bound, S_k the largest deviation of 8 Monte Carlo "
+                    "arithmetic runs at FP32 sizes; rel = |y32 - y64| / s_k",
+            "programs": per}, {
+        "value": op_inst / t_cpu, "unit": "generated op-instances/s", "cores": cores,
+        "kind": "oracle",
+        "sample": f"{sample} instances (+ the last) of each program, FP64 interpreter, {cores} threads"}
+
+
+def other_configs(dev, pk64, pk32, flush, reps, oracle_check=True):
     """Live measurements of the other workloads (cart-pole, MPC, rollout, batch)."""
     import torch
     from concurrent.futures import ThreadPoolExecutor
@@ -175,7 +207,7 @@ def other_configs(dev, pk64, pk32, flush, reps):
         irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(sizes)]
         # ways=4: programs with few instances and many ops (here the 50k-200k-op
         # ones) run as cooperative tiles in the 128-thread scheduler
-        return Batch(irs, [N for _, N in sizes], dtype="f32", ways=4), time.perf_counter() - t0
+        return Batch(irs, [N for _, N in sizes], dtype="f32", ways=4), time.perf_counter() - t0, irs
     ir3 = programs.quadrotor_mpc().to_bytes()
     ir1 = programs.quadrotor_lqr_step().to_bytes()
     srb = programs.srb_step().to_bytes()
@@ -320,7 +352,7 @@ def other_configs(dev, pk64, pk32, flush, reps):
     out["quadrotor_lqr_step_f64"] = rec
 
     # --- C5 uneven batch: 8 random programs, one persistent graph launch vs 8 launches ---
-    b, t_compile = fut["batch"]
+    b, t_compile, batch_irs = fut["batch"]
     xs = [torch.tensor(inputs.normal(64, N, seed=200 + j), dtype=torch.float32, device=dev)
           for j, (_, N) in enumerate(sizes)]
     outs = [torch.empty((32, N), dtype=torch.float32, device=dev) for _, N in sizes]
@@ -337,7 +369,14 @@ def other_configs(dev, pk64, pk32, flush, reps):
     ms_p = _events_ms(lambda: b(xs, outs, mode="persistent"), reps, flush)
     ms_s = _events_ms(lambda: b(xs, outs, mode="plain"), reps, flush)
     gen_ops = sum(n * N for n, N in sizes)
+    fma_eq = sum(peaks.weighted_ops(b.op_counts(j), pk32["weights"]) * N for j, (_, N) in enumerate(sizes))
+    ach = fma_eq / (ms_p * 1e-3)
     out["uneven_batch_f32"] = {
+        "roofline": {"bound": "alu", "achieved": ach * 1e-12, "peak": NOMINAL_FMA_PER_S["f32"] * 1e-12,
+                     "unit": "TFMA/s (FMA-equivalent ops of all 8 programs, FP32)",
+                     "frac": ach / NOMINAL_FMA_PER_S["f32"],
+                     "frac_of_measured": ach / pk32["fma_per_s"],
+                     "work_fma_eq": fma_eq},
         "programs": [{"ops_generated": n, "N": N} for n, N in sizes],
         "op_instances_generated": gen_ops, "persistent_ms": ms_p, "plain_8_launches_ms": ms_s,
         "speedup_persistent_vs_plain": ms_s / ms_p, "tile_block": block,
@@ -347,6 +386,12 @@ def other_configs(dev, pk64, pk32, flush, reps):
                              "4 warps splitting the program; their plain launch runs the same "
                              "cooperative code", **b.info(),
         "gop_per_s_generated": gen_ops / (ms_p * 1e-3) * 1e-9, "setup_seconds": t_compile}
+    if oracle_check:
+        b(xs, outs, mode="persistent")
+        torch.cuda.synchronize()
+        err, cpu = batch_oracle_check(batch_irs, sizes, xs, outs)
+        out["uneven_batch_f32"]["err_vs_fp64_oracle"] = err
+        out["uneven_batch_f32"]["cpu_baseline"] = cpu
     return out
 
 
@@ -570,7 +615,8 @@ def main():
                    "frac_within_1e-12": float(np.mean(rel64 <= 1e-12))}
     extra = None
     if not args.no_configs:
-        extra = other_configs(dev, pk64, pk32, flush, reps=max(args.steps // 2, 5))
+        extra = other_configs(dev, pk64, pk32, flush, reps=max(args.steps // 2, 5),
+                              oracle_check=not args.no_cpu_baseline)
 
     line = {
         "metric": METRIC, "value": value, "unit": "instance-evals/s", "n_gpus": world,

@@ -145,24 +145,45 @@ cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* o
  * in flight). */
 void cusadi_free(cusadi_fn fn);
 
+/* Sizes of a loaded function: its argument counts and stacked non-zeros, the
+ * work-vector length and instruction count of the program file (§III-A: a
+ * function is a work vector plus n_instructions instructions), and what the
+ * passes and the chosen path made of it.  out is written by the library.
+ * Errors: INVALID_ARG for a NULL fn or out. */
 cusadi_status cusadi_info(cusadi_fn fn, cusadi_fn_info* out);
 
-/* Description of input (is_output = 0) or output argument `index`. */
+/* Description of input (is_output = 0) or output argument `index`: shape,
+ * flags, first row in the stacked buffer and the argument's sparsity pattern
+ * (§II-A: CasADi functions compute only the structural non-zeros of sparse
+ * matrices; here the pattern is stored as CSR).  The pointers in *out belong to
+ * the function and live as long as it does.  Errors: INVALID_ARG for a NULL fn
+ * or out, or an index out of range. */
 cusadi_status cusadi_arg_info(cusadi_fn fn, int is_output, int index, cusadi_arg* out);
 
 /* counts[op] = number of ops with that IR op code evaluated per instance, for
- * op < n.  which: 0 forward kernels, 1 adjoint kernels, 2 / 3 the same but
- * only ops tagged FP64 (those a MIXED function evaluates in double). */
+ * op < n: the instruction count by which §IV sizes its benchmark functions,
+ * split by operation so that a roofline can weight each op by its cost.
+ * which: 0 forward kernels, 1 adjoint kernels, 2 / 3 the same but only ops
+ * tagged FP64 (those a MIXED function evaluates in double).  counts (n
+ * entries) is owned by the caller.  Errors: INVALID_ARG for a NULL fn or
+ * counts, n < 0 or which outside 0..3; building the adjoint (which = 1, 3) can
+ * also return COMPILE. */
 cusadi_status cusadi_op_counts(cusadi_fn fn, int which, int64_t* counts, int n);
 
-/* Bytes of device workspace one evaluation of N instances needs: rows for
- * values carried between the kernels of a long program, and for the adjoint
- * one row of per-instance terms for every broadcast input (0 when neither
- * applies).
- * The caller allocates it, 256-byte aligned. */
+/* Bytes of device workspace one evaluation of N instances needs.  CusADi keeps
+ * the whole work vector of every instance in global memory (§III-A, Listing
+ * 2); here values live in registers and only those carried between the
+ * kernels of a long program get workspace rows ([rows x round_up(N, 32)]),
+ * plus, for the adjoint, one row of per-instance terms for every broadcast
+ * input (0 when neither applies).  The caller allocates it, 256-byte aligned,
+ * and owns it.  Returns 0 for a NULL fn, N <= 0, or an adjoint that fails to
+ * build. */
 size_t cusadi_workspace_bytes(cusadi_fn fn, int64_t N, int adjoint);
 
-/* y = f(x) for N instances.  in: [nnz_in x ld_in], out: [nnz_out x ld_out]
+/* y = f(x) for N instances: every instance runs the function's instructions
+ * in order (§III-A; Listing 2 evaluates one instance per GPU thread, here
+ * one thread or, with ways > 1, one group of warps per 32 instances) and
+ * writes only the non-zeros of its outputs.  in: [nnz_in x ld_in], out: [nnz_out x ld_out]
  * device buffers of the dtype's element type; ld_in, ld_out >= N (an input
  * buffer whose rows are all broadcast may use ld_in >= 1).  workspace: at least
  * cusadi_workspace_bytes(fn, N, 0) bytes, or NULL when that is 0.  N = 0 is a
@@ -173,7 +194,10 @@ size_t cusadi_workspace_bytes(cusadi_fn fn, int64_t N, int adjoint);
 cusadi_status cusadi_eval(cusadi_fn fn, const void* in, int64_t ld_in, void* out,
                           int64_t ld_out, int64_t N, void* workspace, cusadi_stream stream);
 
-/* Reverse mode: in_bar = J(x)^T out_bar per instance, J = d out / d in.
+/* Reverse mode: in_bar = J(x)^T out_bar per instance, J = d out / d in
+ * (§II-A: CasADi expressions are differentiable by algorithmic
+ * differentiation; here the reverse sweep is itself a straight-line program,
+ * generated at load and evaluated like the forward one).
  * out_bar: [nnz_out x ld_ob]; in_bar: [nnz_in x ld_ib].  With
  * CUSADI_ADJ_REDUCE_BROADCAST, broadcast input rows receive the sum over
  * instances in column 0: each instance writes its term to the workspace and
@@ -188,13 +212,49 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
                              int64_t ld_ob, void* in_bar, int64_t ld_ib, int64_t N,
                              uint32_t flags, void* workspace, cusadi_stream stream);
 
+/* cusadi_adjoint (reverse mode, §II-A) with the sums over instances of the
+ * broadcast inputs' adjoints (the gradient of a parameter shared by every
+ * instance, such as the feedback gain of a differentiable rollout) written to
+ * a vector of their own instead of column 0 of in_bar: shared_bar[row] for every
+ * broadcast input row `row` (shared_bar has nnz_in entries of the dtype's
+ * element type; other entries are left alone).  Broadcast rows of in_bar are
+ * not written.  The reduction is always on (passing
+ * CUSADI_ADJ_REDUCE_BROADCAST is an INVALID_ARG); with
+ * CUSADI_ADJ_ACCUMULATE_BROADCAST the sums are added to shared_bar, so one
+ * vector collects a shared parameter's gradient over many calls whose in_bar
+ * buffers differ (the steps of a rollout ping-ponging two buffers).  Same
+ * fixed summation order, hence the same bits on every run, as cusadi_adjoint.
+ * Other arguments, ownership and errors as for cusadi_adjoint; INVALID_ARG
+ * also for a NULL shared_bar. */
+cusadi_status cusadi_adjoint_shared(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,
+                                    int64_t ld_ob, void* in_bar, int64_t ld_ib, void* shared_bar,
+                                    int64_t N, uint32_t flags, void* workspace,
+                                    cusadi_stream stream);
+
+/* sums[r] = sum over the N instances of row r of y, for r < rows (with
+ * accumulate != 0: sums[r] += that sum): a batched objective such as the
+ * total loss of a rollout over its environments.  y: [rows x ld_y] device
+ * buffer, ld_y >= N; sums: `rows` device elements; double for CUSADI_F64,
+ * float for CUSADI_F32 and CUSADI_MIXED; both owned by the caller.  One
+ * kernel on `stream`, summing each row in a fixed order (per-thread strided
+ * sums, then a tree), so the result has the same bits on every run.  N = 0
+ * writes zeros (or leaves sums unchanged when accumulating).  The paper has
+ * no counterpart: it keeps such reductions in PyTorch (§III-B).  Errors:
+ * INVALID_ARG for an unknown dtype, rows outside 0..65535, N < 0, NULL
+ * buffers or ld_y < N, checked before any CUDA call; CUDA if the launch
+ * fails. */
+cusadi_status cusadi_sum_instances(int32_t dtype, const void* y, int64_t ld_y, int64_t rows,
+                                   int64_t N, void* sums, int32_t accumulate, cusadi_stream stream);
+
 /* Size of the static scratch region behind cusadi_eval_noalloc, in bytes. */
 #define CUSADI_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 
-/* cusadi_eval for callers that must not allocate device memory: code that
- * runs under a no-allocation rule after start-up (a real-time control loop
- * calling the MPC every tick) or inside a CUDA stream capture, where
- * cudaMalloc is not allowed.  The paper has no counterpart.
+/* cusadi_eval for callers that cannot allocate device memory.  The paper has
+ * no counterpart.  Some callers are not allowed to allocate once they run: a
+ * real-time control loop calling the MPC every tick under a no-allocation rule
+ * (allocation can block for an unbounded time), or a plugin running inside a
+ * host application that owns all device memory and gives the plugin only its
+ * input and output buffers.
  *
  * Same arguments and results as cusadi_eval minus the workspace: the
  * workspace is a file-scope device array of CUSADI_NOALLOC_SCRATCH_BYTES that
@@ -325,6 +385,12 @@ cusadi_status cusadi_batch_set_block(cusadi_batch b, int block);
  * evaluation on this device) and the linked kernel's registers per thread. */
 cusadi_status cusadi_batch_info(cusadi_batch b, int64_t* n_tiles, int32_t* block, int32_t* grid,
                                 int32_t* registers);
+
+/* counts[op] = number of ops with that IR op code that program `prog` of the
+ * batch evaluates per instance (after the passes), for op < n; the weights of
+ * a roofline count (as cusadi_op_counts for one function).  INVALID_ARG for a
+ * NULL batch or counts, or prog outside [0, n_programs). */
+cusadi_status cusadi_batch_op_counts(cusadi_batch b, int prog, int64_t* counts, int n);
 
 /* Waits for all work queued on `stream` with a time limit: OK once it is done,
  * TIMEOUT if it is still running after timeout_seconds (the work is left

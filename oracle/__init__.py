@@ -6,7 +6,8 @@ shared with the CUDA path, and nothing here imports it.
 
 * ``Oracle``      ctypes front of cusadi_oracle.cpp: the plain FP64 sequential
                   interpreter of the IR (CusADi §III-A), FP32/mixed emulation,
-                  the textbook reverse sweep and a first-order rounding bound.
+                  the textbook reverse sweep, a first-order rounding bound
+                  and Monte Carlo arithmetic (randomly perturbed evaluations).
 * ``mp_eval``     the same interpreter in mpmath at high precision (truth for
                   rounding-sensitive pins).
 * ``models``      direct numpy restatements of the benchmark workloads, used to
@@ -42,6 +43,8 @@ def _lib():
         L.orc_adjoint.restype = i32
         L.orc_rounding_bound.argtypes = [vp, dp, i64, dp, i64, i64, i32, i32]
         L.orc_rounding_bound.restype = i32
+        L.orc_eval_perturbed.argtypes = [vp, dp, i64, dp, i64, i64, i32, ctypes.c_uint64, i32]
+        L.orc_eval_perturbed.restype = i32
         _LIB = L
     return _LIB
 
@@ -114,14 +117,43 @@ class Oracle:
             raise OracleError(f"orc_rounding_bound failed ({rc})")
         return B
 
+    def eval_perturbed(self, x, kind: int = 1, seed: int = 0, threads: int = 0) -> np.ndarray:
+        """One Monte Carlo arithmetic run at FP32 sizes: FP64 evaluation with
+        every result and stored output multiplied by (1 + eps_t * xi), xi
+        uniform in [-1, 1) drawn per (seed, instance, instruction), eps_t as in
+        rounding_bound(kind=1).  Only kind 1 exists: perturbations of FP64 size
+        would drown in double's own rounding."""
+        x = self._x(x)
+        N = x.shape[1]
+        y = np.zeros((self.nnz_out, N), dtype=np.float64)
+        rc = _lib().orc_eval_perturbed(self._h, _dp(x), N, _dp(y), N, N, kind, seed, threads)
+        if rc:
+            raise OracleError(f"orc_eval_perturbed failed ({rc})")
+        return y
 
-def tolerance(oracle: Oracle, x, y_ref, tau: float, kind: int, kappa: float = 2.0):
-    """Per-element tolerance max(tau * s_k, kappa * B_k,i) with s_k = max_i |y_k,i|.
+    def mca_spread(self, x, y_ref, kind: int, runs: int = 8, seed: int = 1) -> np.ndarray:
+        """max over `runs` Monte Carlo arithmetic runs of |y_run - y_ref|."""
+        spread = np.zeros_like(y_ref)
+        for r in range(runs):
+            spread = np.fmax(spread, np.abs(self.eval_perturbed(x, kind, seed + r) - y_ref))
+        return spread
+
+
+def tolerance(oracle: Oracle, x, y_ref, tau: float, kind: int, kappa: float = 2.0,
+              mca_runs: int = 0, kappa_mca: float = 4.0):
+    """Per-element tolerance max(tau * s_k, kappa * B_k,i [, kappa_mca * S_k])
+    with s_k = max_i |y_k,i|.
 
     tau is the stated relative tolerance (1e-12 FP64, 2e-4 FP32) scaled by the
     output's magnitude; B is the first-order rounding bound of the program at
     that instance, which dominates only where the program is deep enough that
-    no correct implementation can meet tau.
+    no correct implementation can meet tau.  With mca_runs > 0, S_k is the
+    largest deviation from y_ref, over the instances of output row k, of that
+    many Monte Carlo arithmetic runs: where errors have grown so large that the
+    first-order bound no longer holds (a perturbed operand reaching a
+    stationary point of the next operation, or a deep output with no correct
+    digit left), S_k still measures how far a correct evaluation with rounding
+    errors of the same size lands on that output.
     """
     s = np.max(np.abs(y_ref), axis=1, keepdims=True)
     B = oracle.rounding_bound(x, kind=kind)
@@ -129,4 +161,8 @@ def tolerance(oracle: Oracle, x, y_ref, tau: float, kind: int, kappa: float = 2.
         B = B + np.ldexp(1.0, -24) * np.abs(y_ref)
     # where the bound is undefined (a derivative blows up at a discontinuity of
     # the program) only the stated relative tolerance applies
-    return np.fmax(tau * s, kappa * B)
+    tol = np.fmax(tau * s, kappa * B)
+    if mca_runs:
+        S = oracle.mca_spread(x, y_ref, kind, runs=mca_runs)
+        tol = np.fmax(tol, kappa_mca * np.max(S, axis=1, keepdims=True))
+    return tol

@@ -30,6 +30,22 @@
 // relative error of instruction t (Higham, Accuracy and Stability of Numerical
 // Algorithms, 2nd ed., §3.1 and Ch. 3's running error analysis).  It is computed
 // with one reverse sweep per output.
+//
+// Monte Carlo arithmetic (D. S. Parker, "Monte Carlo Arithmetic: exploiting
+// randomness in floating-point arithmetic", UCLA CSD-970002, 1997): the program
+// is evaluated in FP64 with each instruction's result multiplied by
+// (1 + eps_t * xi), xi uniform in [-1, 1), eps_t the same per-instruction
+// relative error as in the rounding bound.  The spread of a few such runs around
+// the unperturbed value estimates how far another evaluation with rounding
+// errors of that size can land, including the nonlinear effects that a
+// first-order bound leaves out (a perturbed operand at a stationary point of
+// exp(-a^2), for instance).  Only FP32-sized perturbations (u = 2^-24) are
+// offered: double carries them with 29 bits to spare, whereas perturbations of
+// FP64 size would be lost in double's own rounding (1 + 2^-53 xi rounds to one
+// of three values).  xi comes from a counter-based generator: the
+// SplitMix64 output function (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014) applied to a key made of the
+// seed, the instance and the instruction index.
 
 #include <cmath>
 #include <cstdint>
@@ -370,6 +386,48 @@ double ulp_gpu(int op, bool f32) {
   }
 }
 
+
+// Relative error eps_t of each instruction for the rounding bound and for
+// Monte Carlo arithmetic.
+// kind 0: eps_t bounds |GPU FP64 - oracle FP64| (GPU ulp table + up to 2 ulp for
+//         the host libm, u = 2^-53 per correctly rounded op on each side).
+// kind 1: eps_t bounds |GPU FP32 - exact| (u = 2^-24, GPU FP32 ulp table,
+//         plus the rounding of inputs and constants to float).
+std::vector<double> op_eps(const OProgram& P, int kind) {
+  const size_t n = P.code.size();
+  std::vector<double> eps(n, 0.0);
+  for (size_t t = 0; t < n; ++t) {
+    const OInstr& I = P.code[t];
+    if (kind == 0) {
+      const double u = std::ldexp(1.0, -53);
+      if (I.op == O_INPUT || I.op == O_CONST || I.op == O_OUTPUT || I.op == O_ASSIGN) eps[t] = 0;
+      else if (ulp_gpu(I.op, false) > 0.5) eps[t] = 2 * u * ulp_gpu(I.op, false) + 4 * u;  // host <= 2 ulp
+      else eps[t] = 2 * u;  // correctly rounded on both sides
+    } else {
+      const double u = std::ldexp(1.0, -24);
+      if (I.op == O_OUTPUT || I.op == O_ASSIGN) eps[t] = 0;
+      else if (I.op == O_INPUT || I.op == O_CONST) eps[t] = u;
+      else eps[t] = 2 * u * ulp_gpu(I.op, true);
+    }
+  }
+  return eps;
+}
+
+// SplitMix64's output function of a 64-bit key.
+inline uint64_t splitmix64_mix(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Uniform in [-1, 1) for (seed, instance i, instruction t).
+inline double mca_xi(uint64_t seed, int64_t i, size_t t) {
+  uint64_t key = splitmix64_mix(seed) ^ (((uint64_t)i << 32) | (uint64_t)(t & 0xffffffffu));
+  uint64_t z = splitmix64_mix(key);
+  return (double)(z >> 11) * std::ldexp(1.0, -52) - 1.0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -425,30 +483,13 @@ int orc_adjoint(orc_prog* h, const double* x, int64_t ld_x, const double* ybar, 
   return 0;
 }
 
-// Per output k and instance i: B[k, i] = sum_t |d y_k / d v_t| * eps_t * |v_t|.
-// kind 0: eps_t bounds |GPU FP64 - oracle FP64| (GPU ulp table + up to 2 ulp for
-//         the host libm, u = 2^-53 per correctly rounded op on each side).
-// kind 1: eps_t bounds |GPU FP32 - exact| (u = 2^-24, GPU FP32 ulp table,
-//         plus the rounding of inputs and constants to float).
+// Per output k and instance i: B[k, i] = sum_t |d y_k / d v_t| * eps_t * |v_t|,
+// eps_t from op_eps (kind 0: FP64 GPU vs oracle; kind 1: FP32 GPU vs exact).
 int orc_rounding_bound(orc_prog* h, const double* x, int64_t ld_x, double* B, int64_t ld_b,
                        int64_t N, int kind, int n_threads) {
   const OProgram& P = h->P;
   const size_t n = P.code.size();
-  std::vector<double> eps(n, 0.0);
-  for (size_t t = 0; t < n; ++t) {
-    const OInstr& I = P.code[t];
-    if (kind == 0) {
-      const double u = std::ldexp(1.0, -53);
-      if (I.op == O_INPUT || I.op == O_CONST || I.op == O_OUTPUT || I.op == O_ASSIGN) eps[t] = 0;
-      else if (ulp_gpu(I.op, false) > 0.5) eps[t] = 2 * u * ulp_gpu(I.op, false) + 4 * u;  // host <= 2 ulp
-      else eps[t] = 2 * u;  // correctly rounded on both sides
-    } else {
-      const double u = std::ldexp(1.0, -24);
-      if (I.op == O_OUTPUT || I.op == O_ASSIGN) eps[t] = 0;
-      else if (I.op == O_INPUT || I.op == O_CONST) eps[t] = u;
-      else eps[t] = 2 * u * ulp_gpu(I.op, true);
-    }
-  }
+  const std::vector<double> eps = op_eps(P, kind);
   parallel_for(N, n_threads, [&](int64_t lo, int64_t hi) {
     std::vector<double> w(std::max<uint32_t>(P.n_work, 1)), wb(w.size());
     std::vector<double> tape(3 * n + 1), yb(P.nnz_out, 0.0);
@@ -460,6 +501,43 @@ int orc_rounding_bound(orc_prog* h, const double* x, int64_t ld_x, double* B, in
         B[(int64_t)k * ld_b + i] = reverse_instance(P, tape.data(), yb.data(), wb.data(), nullptr,
                                                     eps.data());
         yb[k] = 0.0;
+      }
+    }
+  });
+  return 0;
+}
+
+// Monte Carlo arithmetic run `seed` at FP32 sizes: FP64 evaluation in which
+// every instruction's result and every stored output is multiplied by
+// (1 + eps_t * xi), eps_t from op_eps(kind 1) (u for outputs) and
+// xi = mca_xi(seed, i, t).  Only kind 1 is accepted.
+int orc_eval_perturbed(orc_prog* h, const double* x, int64_t ld_x, double* y, int64_t ld_y,
+                       int64_t N, int kind, uint64_t seed, int n_threads) {
+  const OProgram& P = h->P;
+  if (kind != 1) return 1;
+  const std::vector<double> eps = op_eps(P, kind);
+  const double u_out = std::ldexp(1.0, -24);
+  parallel_for(N, n_threads, [&](int64_t lo, int64_t hi) {
+    std::vector<double> w(std::max<uint32_t>(P.n_work, 1));
+    for (int64_t i = lo; i < hi; ++i) {
+      for (size_t t = 0; t < P.code.size(); ++t) {
+        const OInstr& I = P.code[t];
+        double res;
+        if (I.op == O_INPUT) {
+          res = x[(int64_t)I.a * ld_x + (P.in_bcast[I.a] ? 0 : i)];
+        } else if (I.op == O_CONST) {
+          res = P.k[I.a];
+        } else if (I.op == O_OUTPUT) {
+          double v = w[I.a];
+          v *= 1.0 + u_out * mca_xi(seed, i, t);
+          y[(int64_t)I.out * ld_y + i] = v;
+          continue;
+        } else {
+          double va = w[I.a], vb = arity(I.op) == 2 ? w[I.b] : 0.0;
+          res = apply(I.op, va, vb, I.op == O_FMA_CONST ? P.k[I.c] : 0.0);
+        }
+        if (eps[t] > 0) res *= 1.0 + eps[t] * mca_xi(seed, i, t);
+        w[I.out] = res;
       }
     }
   });

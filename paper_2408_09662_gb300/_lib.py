@@ -76,6 +76,10 @@ SIGNATURES = {
     "cusadi_eval": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
     "cusadi_adjoint": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                  c_int64, c_uint32, c_void_p, c_void_p]),
+    "cusadi_adjoint_shared": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
+                                        c_void_p, c_int64, c_uint32, c_void_p, c_void_p]),
+    "cusadi_sum_instances": (c_int32, [c_int32, c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int32,
+                                       c_void_p]),
     "cusadi_eval_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_void_p]),
     "cusadi_debug_count": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "cusadi_densify": (c_int32, [c_void_p, ctypes.c_int, c_void_p, c_int64, c_void_p, c_int64, c_int64,
@@ -95,6 +99,7 @@ SIGNATURES = {
                                     ctypes.c_int, c_void_p]),
     "cusadi_batch_info": (c_int32, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int32),
                                     ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "cusadi_batch_op_counts": (c_int32, [c_void_p, ctypes.c_int, ctypes.POINTER(c_int64), ctypes.c_int]),
     "cusadi_status_string": (c_char_p, [c_int32]),
     "cusadi_last_error": (c_char_p, []),
 }
@@ -177,6 +182,19 @@ def cusadi_adjoint(fn: int, inp: int, ld_in: int, out_bar: int, ld_ob: int, in_b
                                workspace, stream), "cusadi_adjoint")
 
 
+def cusadi_adjoint_shared(fn: int, inp: int, ld_in: int, out_bar: int, ld_ob: int, in_bar: int,
+                          ld_ib: int, shared_bar: int, N: int, flags: int, workspace: int,
+                          stream: int) -> None:
+    check(lib().cusadi_adjoint_shared(fn, inp, ld_in, out_bar, ld_ob, in_bar, ld_ib, shared_bar, N,
+                                      flags, workspace, stream), "cusadi_adjoint_shared")
+
+
+def cusadi_sum_instances(dtype: int, y: int, ld_y: int, rows: int, N: int, sums: int,
+                         accumulate: bool, stream: int) -> None:
+    check(lib().cusadi_sum_instances(dtype, y, ld_y, rows, N, sums, int(accumulate), stream),
+          "cusadi_sum_instances")
+
+
 def cusadi_eval_noalloc(fn: int, inp: int, ld_in: int, out: int, ld_out: int, N: int,
                         stream: int) -> None:
     check(lib().cusadi_eval_noalloc(fn, inp, ld_in, out, ld_out, N, stream), "cusadi_eval_noalloc")
@@ -248,3 +266,9 @@ def cusadi_batch_info(b: int) -> tuple:
     check(lib().cusadi_batch_info(b, ctypes.byref(nt), ctypes.byref(blk), ctypes.byref(grid),
                                   ctypes.byref(regs)), "cusadi_batch_info")
     return nt.value, blk.value, grid.value, regs.value
+
+
+def cusadi_batch_op_counts(b: int, prog: int, n: int = 64) -> list:
+    arr = (c_int64 * n)()
+    check(lib().cusadi_batch_op_counts(b, prog, arr, n), "cusadi_batch_op_counts")
+    return list(arr)

@@ -171,9 +171,14 @@ class Function:
 
     def adjoint(self, x: torch.Tensor, ybar: torch.Tensor, out: torch.Tensor | None = None,
                 accumulate: bool = False, reduce_broadcast: bool = False,
-                accumulate_broadcast: bool = False) -> torch.Tensor:
+                accumulate_broadcast: bool = False,
+                shared_out: torch.Tensor | None = None) -> torch.Tensor:
         """x_bar = J(x)^T y_bar per instance (broadcast rows summed when reduce_broadcast;
-        accumulate_broadcast adds those sums into out instead of overwriting them)."""
+        accumulate_broadcast adds those sums into out instead of overwriting them).
+        With shared_out (a CUDA vector of nnz_in entries), the broadcast rows'
+        sums go to shared_out[row] instead (cusadi_adjoint_shared: always
+        reduced, accumulated when accumulate_broadcast) and their rows of out
+        are not written."""
         self._check(x, self.nnz_in, "x")
         N = x.shape[1]
         self._check(ybar, self.nnz_out, "ybar")
@@ -182,14 +187,43 @@ class Function:
                 (self.nnz_in, N), dtype=self.torch_dtype, device=x.device)
         self._check(out, self.nnz_in, "out")
         flags = (L.CUSADI_ADJ_ACCUMULATE if accumulate else 0) | \
-                (L.CUSADI_ADJ_REDUCE_BROADCAST if reduce_broadcast else 0) | \
                 (L.CUSADI_ADJ_ACCUMULATE_BROADCAST if accumulate_broadcast else 0)
         ws = self.workspace(N, True, x.device)
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        if shared_out is not None:
+            if not shared_out.is_cuda or shared_out.dtype != self.torch_dtype or \
+                    shared_out.numel() != self.nnz_in or not shared_out.is_contiguous():
+                raise ValueError(f"shared_out must be a contiguous CUDA vector of {self.nnz_in} "
+                                 f"{self.torch_dtype} entries")
+            L.cusadi_adjoint_shared(self._fn, x.data_ptr(), self._ld(x), ybar.data_ptr(),
+                                    self._ld(ybar), out.data_ptr(), self._ld(out),
+                                    shared_out.data_ptr(), N, flags,
+                                    ws.data_ptr() if ws is not None else 0, stream)
+            return out
+        if reduce_broadcast:
+            flags |= L.CUSADI_ADJ_REDUCE_BROADCAST
         L.cusadi_adjoint(self._fn, x.data_ptr(), self._ld(x), ybar.data_ptr(), self._ld(ybar),
                          out.data_ptr(), self._ld(out), N, flags,
-                         ws.data_ptr() if ws is not None else 0,
-                         torch.cuda.current_stream(x.device).cuda_stream)
+                         ws.data_ptr() if ws is not None else 0, stream)
         return out
+
+
+def sum_instances(y: torch.Tensor, out: torch.Tensor | None = None,
+                  accumulate: bool = False) -> torch.Tensor:
+    """Per-row sums over the instances of a [rows, N] CUDA tensor (float32 or
+    float64), computed by the library in a fixed order (cusadi_sum_instances):
+    the same bits on every run."""
+    if not y.is_cuda or y.dim() != 2 or y.stride(1) != 1 or y.dtype not in (torch.float32, torch.float64):
+        raise ValueError("y must be a [rows, N] float32/float64 CUDA tensor with unit stride along N")
+    rows, N = y.shape
+    if out is None:
+        out = (torch.zeros if accumulate else torch.empty)(rows, dtype=y.dtype, device=y.device)
+    if not out.is_cuda or out.dtype != y.dtype or out.numel() != rows or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA vector with one entry per row of y")
+    dt = L.CUSADI_F64 if y.dtype == torch.float64 else L.CUSADI_F32
+    L.cusadi_sum_instances(dt, y.data_ptr(), Function._ld(y), rows, N, out.data_ptr(), accumulate,
+                           torch.cuda.current_stream(y.device).cuda_stream)
+    return out
 
 
 class _Apply(torch.autograd.Function):
@@ -286,6 +320,10 @@ class Batch:
     def set_block(self, block: int) -> None:
         L.cusadi_batch_set_block(self._b, block)
         self.block = block
+
+    def op_counts(self, j: int) -> list:
+        """Per-op-code counts of the ops program j evaluates per instance."""
+        return L.cusadi_batch_op_counts(self._b, j)
 
     def workspace(self, device) -> torch.Tensor | None:
         """One workspace kept for the batch: calls on one batch must not overlap

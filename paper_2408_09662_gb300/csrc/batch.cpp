@@ -536,4 +536,14 @@ cusadi_status cusadi_batch_info(cusadi_batch b, int64_t* n_tiles, int32_t* block
   return CUSADI_OK;
 }
 
+cusadi_status cusadi_batch_op_counts(cusadi_batch b, int prog, int64_t* counts, int n) {
+  if (!b || !counts || n < 0) return bfail(CUSADI_E_INVALID_ARG, "NULL argument");
+  if (prog < 0 || prog >= (int)b->progs.size())
+    return bfail(CUSADI_E_INVALID_ARG, "program index out of range");
+  std::vector<int64_t> h;
+  op_histogram(b->progs[prog].g, h);
+  for (int i = 0; i < n; ++i) counts[i] = i < (int)h.size() ? h[i] : 0;
+  return CUSADI_OK;
+}
+
 }  // extern "C"

@@ -165,6 +165,10 @@ int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, con
 int launch_reduce_finish(int dtype, const void* Wr, int64_t ldr, int64_t N, const int64_t* rows,
                          int64_t n_rows, void* Y, int64_t ldy, int accumulate, void* stream);
 // threads per block of the shared-memory interpreter (0: work vector too long)
+// S[r] (+)= sum over the N instances of row r of Y, rows 0..rows-1, in a fixed
+// order; dtype CUSADI_F64 sums doubles, otherwise floats.
+int launch_sum_rows(int dtype, const void* Y, int64_t ldy, int64_t rows, int64_t N, void* S,
+                    int accumulate, void* stream);
 int interp_block(int64_t n_slots, int dtype);
 // dense copy of one output argument (kernels.cu); returns a cudaError_t value
 int launch_densify(int dtype, const void* y, int64_t ldy, int64_t off, const int32_t* map,

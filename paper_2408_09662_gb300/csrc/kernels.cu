@@ -155,6 +155,25 @@ __global__ void __launch_bounds__(512) reduce_finish_kernel(const S* __restrict_
   }
 }
 
+// One CTA per row of Y: S[r] = sum over j < N of Y[r * ldy + j], in the same
+// order as reduce_finish_kernel (strided per-thread sums, then a tree).
+template <typename T>
+__global__ void __launch_bounds__(512) sum_rows_kernel(const T* __restrict__ Y, long long ldy,
+                                                       long long N, T* __restrict__ S,
+                                                       int accumulate) {
+  __shared__ T s_[512];
+  const T* __restrict__ P = Y + (long long)blockIdx.x * ldy;
+  T a = 0;
+  for (long long j = threadIdx.x; j < N; j += 512) a += P[j];
+  s_[threadIdx.x] = a;
+  __syncthreads();
+  for (int d = 256; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) s_[threadIdx.x] += s_[threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) S[blockIdx.x] = accumulate ? S[blockIdx.x] + s_[0] : s_[0];
+}
+
 }  // namespace
 
 // Threads per block for the shared-memory work vector (0: it does not fit).
@@ -230,6 +249,19 @@ int launch_reduce_finish(int dtype, const void* Wr, int64_t ldr, int64_t N, cons
   else
     reduce_finish_kernel<float, double><<<(unsigned)n_rows, 512, 0, st>>>(
         (const double*)Wr, ldr, N, rows, (float*)Y, ldy, accumulate);
+  return (int)cudaGetLastError();
+}
+
+int launch_sum_rows(int dtype, const void* Y, int64_t ldy, int64_t rows, int64_t N, void* S,
+                    int accumulate, void* stream) {
+  if (rows <= 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == CUSADI_F64)
+    sum_rows_kernel<double><<<(unsigned)rows, 512, 0, st>>>((const double*)Y, ldy, N, (double*)S,
+                                                            accumulate);
+  else
+    sum_rows_kernel<float><<<(unsigned)rows, 512, 0, st>>>((const float*)Y, ldy, N, (float*)S,
+                                                           accumulate);
   return (int)cudaGetLastError();
 }
 

@@ -1,7 +1,9 @@
 // Allocation-free evaluation: the workspace is a static device array.
 //
-// For callers that may not allocate device memory once they run (a control
-// loop with a no-allocation rule, or code inside a CUDA stream capture).  The
+// For callers that cannot allocate device memory once they run: a real-time
+// control loop under a no-allocation rule (an allocation can block for an
+// unbounded time), or a plugin whose host application owns all device memory
+// and hands it only input and output buffers.  The
 // array below is reserved on every GPU that loads this library and stays until
 // the process exits.  In host code its name is only a host-side stand-in, so
 // its device address is looked up once per device with cudaGetSymbolAddress.

@@ -844,9 +844,15 @@ cusadi_status cusadi_eval_host(cusadi_fn fn, const void* in_host, int64_t ld_in,
   return CUSADI_OK;
 }
 
-cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,
-                             int64_t ld_ob, void* in_bar, int64_t ld_ib, int64_t N,
-                             uint32_t flags, void* workspace, cusadi_stream stream) {
+}  // extern "C"
+
+namespace {
+
+// Reverse mode with the broadcast rows' sums written to shared_bar[row] when
+// shared_bar is given (else to column 0 of in_bar's broadcast rows).
+cusadi_status adjoint_impl(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,
+                           int64_t ld_ob, void* in_bar, int64_t ld_ib, void* shared_bar, int64_t N,
+                           uint32_t flags, void* workspace, cusadi_stream stream) {
   if (!fn) return fail(CUSADI_E_INVALID_ARG, "fn is NULL");
   if (N < 0) return fail(CUSADI_E_INVALID_ARG, "N must be >= 0");
   if (flags & ~(CUSADI_ADJ_ACCUMULATE | CUSADI_ADJ_REDUCE_BROADCAST | CUSADI_ADJ_ACCUMULATE_BROADCAST))
@@ -868,6 +874,10 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
   const int acc = (flags & CUSADI_ADJ_ACCUMULATE) ? 1 : 0;
   const bool has_reduce = fn->path == CUSADI_PATH_INTERP ? fn->adj.ip.has_reduce : fn->adj.cg.has_reduce;
   const bool acc_bcast = acc || (flags & CUSADI_ADJ_ACCUMULATE_BROADCAST);
+  // destination of the broadcast rows' sums: element `row` of shared_bar, or
+  // column 0 of row `row` of in_bar
+  void* sum_dst = shared_bar ? shared_bar : in_bar;
+  const int64_t sum_ld = shared_bar ? 1 : ld_ib;
   s = run(fn, fn->adj, *ds, true, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, N, workspace, acc,
           reduce ? 1 : 0, stream);
   if (s != CUSADI_OK || !reduce || !has_reduce) return s;
@@ -878,16 +888,53 @@ cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const 
     const size_t off = (interp_block(ip.n_slots, fn->opt.dtype) > 0 ? 0 : (size_t)ip.n_slots * interp_ldw(N)) *
                        elt_ws(fn->opt.dtype);
     int rc = launch_reduce_finish(fn->opt.dtype, (char*)workspace + off, round_up(N, 32), N, ds->d_reduce_rows,
-                                  (int64_t)ip.reduce_rows.size(), in_bar, ld_ib, acc_bcast ? 1 : 0, stream);
+                                  (int64_t)ip.reduce_rows.size(), sum_dst, sum_ld, acc_bcast ? 1 : 0,
+                                  stream);
     if (rc != 0) return fail(CUSADI_E_CUDA, std::string("reduction launch: ") + cudaGetErrorString((cudaError_t)rc));
     return CUSADI_OK;
   }
-  long long lw = round_up(N, 32), n = N, ly = ld_ib;
+  long long lw = round_up(N, 32), n = N, ly = sum_ld;
   int accumulate = acc_bcast ? 1 : 0;
-  void* args[] = {&workspace, &lw, &n, &in_bar, &ly, &accumulate};
+  void* args[] = {&workspace, &lw, &n, &sum_dst, &ly, &accumulate};
   CUresult r = driver().launchKernel(ds->adj_finish, (unsigned)fn->adj.cg.reduce_rows.size(), 1, 1, 512, 1, 1,
                                      0, (CUstream)stream, args, nullptr);
   if (r != CUDA_SUCCESS) return cuda_fail("cuLaunchKernel", r);
+  return CUSADI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cusadi_status cusadi_adjoint(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,
+                             int64_t ld_ob, void* in_bar, int64_t ld_ib, int64_t N,
+                             uint32_t flags, void* workspace, cusadi_stream stream) {
+  return adjoint_impl(fn, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, nullptr, N, flags, workspace,
+                      stream);
+}
+
+cusadi_status cusadi_adjoint_shared(cusadi_fn fn, const void* in, int64_t ld_in, const void* out_bar,
+                                    int64_t ld_ob, void* in_bar, int64_t ld_ib, void* shared_bar,
+                                    int64_t N, uint32_t flags, void* workspace,
+                                    cusadi_stream stream) {
+  if (!shared_bar) return fail(CUSADI_E_INVALID_ARG, "shared_bar is NULL");
+  if (flags & CUSADI_ADJ_REDUCE_BROADCAST)
+    return fail(CUSADI_E_INVALID_ARG, "cusadi_adjoint_shared always reduces: do not pass "
+                                      "CUSADI_ADJ_REDUCE_BROADCAST");
+  return adjoint_impl(fn, in, ld_in, out_bar, ld_ob, in_bar, ld_ib, shared_bar, N,
+                      flags | CUSADI_ADJ_REDUCE_BROADCAST, workspace, stream);
+}
+
+cusadi_status cusadi_sum_instances(int32_t dtype, const void* y, int64_t ld_y, int64_t rows,
+                                   int64_t N, void* sums, int32_t accumulate, cusadi_stream stream) {
+  if (dtype < CUSADI_F64 || dtype > CUSADI_MIXED) return fail(CUSADI_E_INVALID_ARG, "unknown dtype");
+  if (rows < 0 || N < 0) return fail(CUSADI_E_INVALID_ARG, "rows and N must be >= 0");
+  if (rows == 0) return CUSADI_OK;
+  if (rows > 65535) return fail(CUSADI_E_INVALID_ARG, "at most 65,535 rows per call");
+  if (!sums || (N > 0 && !y)) return fail(CUSADI_E_INVALID_ARG, "y / sums is NULL");
+  if (N > 0 && ld_y < N) return fail(CUSADI_E_INVALID_ARG, "ld_y smaller than N");
+  int rc = launch_sum_rows(dtype, y, ld_y, rows, N, sums, accumulate ? 1 : 0, stream);
+  if (rc != 0) return fail(CUSADI_E_CUDA, std::string("sum launch: ") + cudaGetErrorString((cudaError_t)rc));
   return CUSADI_OK;
 }
 

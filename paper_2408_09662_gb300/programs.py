@@ -16,8 +16,9 @@ from .ir import Instr, Op, ProgramIR, Sparsity
 # Listing 2 / Fig. 2: y = (sin x + x)^2, with in-place slot reuse
 # ---------------------------------------------------------------------------
 def listing2() -> ProgramIR:
-    """The example function of Fig. 2 exactly as Listing 2 evaluates it:
-    w0 = x; w1 = sin(w0); w1 = w1 + w0; w1 = w1 * w1; y = w1."""
+    """The example function of Fig. 2 (§III-A), y = (sin x + x)^2, as a two-slot
+    work vector: slot 0 holds x, slot 1 holds sin x and then, reused in place,
+    the sum and its square, which is the output."""
     ins = [Instr(Op.INPUT, 0, 0), Instr(Op.SIN, 1, 0), Instr(Op.ADD, 1, 1, 0),
            Instr(Op.MUL, 1, 1, 1), Instr(Op.OUTPUT, 0, 1)]
     return ProgramIR(2, [Sparsity.dense(1, 1, "x")], [Sparsity.dense(1, 1, "y")], ins, [])

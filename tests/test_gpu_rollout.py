@@ -105,6 +105,111 @@ def test_step_adjoint_matches_oracle_reverse_sweep(prog64):
     np.testing.assert_allclose(xb[:144, 0], Kref, rtol=1e-11, atol=1e-12 * np.max(np.abs(Kref)))
 
 
+def test_fp32_step_adjoint_matches_oracle_reverse_sweep():
+    """The FP32 adjoint kernel of one SRB step against the oracle's FP64 reverse
+    sweep on the same FP32-rounded inputs, under the FP32 rule: per input row
+    k, 2e-4 of the row's largest adjoint; for the shared gain reduced over the
+    2,048 instances, 2e-4 of the sum of the magnitudes it adds up."""
+    N = 2048
+    x0, K = srb_inputs(N, seed=14)
+    X = np.vstack([np.tile(K.reshape(144, 1), (1, N)), x0, np.zeros((1, N))])
+    X = X.astype(np.float32).astype(np.float64)
+    ybar = np.random.default_rng(15).standard_normal((13, N)).astype(np.float32).astype(np.float64)
+    ref = Oracle(programs.srb_step().to_bytes()).adjoint(X, ybar)
+    fn = Function(programs.srb_step(), dtype="f32")
+    xb = fn.adjoint(torch.tensor(X, dtype=torch.float32, device="cuda"),
+                    torch.tensor(ybar, dtype=torch.float32, device="cuda"),
+                    reduce_broadcast=True).double().cpu().numpy()
+    s = np.max(np.abs(ref[144:]), axis=1, keepdims=True)
+    assert np.all(np.abs(xb[144:] - ref[144:]) <= 2e-4 * s)
+    Kref = ref[:144].sum(axis=1)
+    scale = np.abs(ref[:144]).sum(axis=1)
+    assert np.all(np.abs(xb[:144, 0] - Kref) <= 2e-4 * scale)
+
+
+def _oracle_rollout_gradient(x0, K, steps):
+    """dL/dx0 and dL/dK of the rollout from the oracle alone: FP64 forward steps
+    with every state kept, then the oracle's reverse sweep of each step in
+    reverse order, the shared gain's per-instance adjoints summed over
+    instances and steps."""
+    orc = Oracle(programs.srb_step().to_bytes())
+    N = x0.shape[1]
+    X = np.vstack([np.tile(K.reshape(144, 1), (1, N)), x0, np.zeros((1, N))])
+    states = []
+    for _ in range(steps):
+        states.append(X.copy())
+        X[144:] = orc.eval(X)
+    ybar = np.zeros((13, N))
+    ybar[12] = 1.0                        # dL/dL_T; the final states carry no gradient
+    gK = np.zeros(144)
+    for X in reversed(states):
+        xb = orc.adjoint(X, ybar)
+        gK += xb[:144].sum(axis=1)
+        ybar = xb[144:]
+    return ybar[:12], gK.reshape(12, 12)
+
+
+def test_fp32_rollout_gradient_against_oracle():
+    """50 steps in FP32 through the checkpointed reverse pass against the
+    oracle's FP64 reverse sweeps on the same FP32-rounded x0 and K: per state
+    row, 2e-4 of the row's largest gradient; the gain, 2e-4 of its largest
+    entry."""
+    x0, K = srb_inputs(256, seed=16)
+    x0 = x0.astype(np.float32).astype(np.float64)
+    K = K.astype(np.float32).astype(np.float64)
+    prog32 = StepProgram(Function(programs.srb_step(), dtype="f32"), 144, 12)
+    _, _, gx, gK = _grad(prog32, x0, K, 10)
+    rgx, rgK = _oracle_rollout_gradient(x0, K, STEPS)
+    s = np.max(np.abs(rgx), axis=1, keepdims=True)
+    rel_x = float(np.max(np.abs(gx - rgx) / s))
+    rel_K = float(np.max(np.abs(gK - rgK)) / np.max(np.abs(rgK)))
+    assert rel_x <= 2e-4 and rel_K <= 2e-4, (rel_x, rel_K)
+
+
+def test_adjoint_shared_equals_reduced_rows_bitwise():
+    """cusadi_adjoint_shared writes the same sums, bit for bit, to its own
+    vector that cusadi_adjoint with the reduction writes to column 0 of the
+    broadcast rows, leaves those rows of in_bar alone, and accumulates."""
+    fn = Function(programs.srb_step(), dtype="f64")
+    N = 3000
+    x0, K = srb_inputs(N, seed=17)
+    X = torch.tensor(np.vstack([np.tile(K.reshape(144, 1), (1, N)), x0, np.zeros((1, N))]), device="cuda")
+    ybar = torch.tensor(np.random.default_rng(18).standard_normal((13, N)), device="cuda")
+    red = fn.adjoint(X, ybar, reduce_broadcast=True)
+    out = torch.full((157, N), 7.0, dtype=torch.float64, device="cuda")
+    shared = torch.full((157,), -1.0, dtype=torch.float64, device="cuda")
+    fn.adjoint(X, ybar, out=out, shared_out=shared)
+    torch.cuda.synchronize()
+    assert torch.equal(shared[:144], red[:144, 0])
+    assert torch.all(shared[144:] == -1.0) and torch.all(out[:144] == 7.0)
+    assert torch.equal(out[144:], red[144:])
+    fn.adjoint(X, ybar, out=out, shared_out=shared, accumulate_broadcast=True)
+    torch.cuda.synchronize()
+    assert torch.equal(shared[:144], red[:144, 0] + red[:144, 0])
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_sum_instances_is_reproducible_and_accurate(dtype):
+    from paper_2408_09662_gb300.api import sum_instances
+    rng = np.random.default_rng(19)
+    y = rng.standard_normal((5, 100003))
+    yt = torch.tensor(y, dtype=dtype, device="cuda")
+    a, b = sum_instances(yt), sum_instances(yt)
+    c = sum_instances(yt, out=a.clone(), accumulate=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(c, a + a)
+    exact = y.astype(np.float32 if dtype == torch.float32 else np.float64).astype(np.float64).sum(axis=1)
+    u = 2.0 ** (-24 if dtype == torch.float32 else -53)
+    bound = (200 + 9) * u * np.abs(y).sum(axis=1)      # per-thread chains of <= 196, tree of 9
+    assert np.all(np.abs(a.double().cpu().numpy() - exact) <= bound)
+
+
+def test_rollout_loss_sum_is_bitwise_reproducible(prog64):
+    x0, K = srb_inputs(4096, seed=20)
+    Ls = [_grad(prog64, x0, K, 10)[0] for _ in range(3)]
+    assert Ls[0] == Ls[1] == Ls[2]
+
+
 def test_checkpointing_does_not_change_the_gradient(prog64):
     x0, K = srb_inputs(512, seed=6)
     L1, _, gx1, gK1 = _grad(prog64, x0, K, 10)

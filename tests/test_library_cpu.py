@@ -30,6 +30,19 @@ def test_library_exports_every_declared_entry_point():
     assert set(names) <= set(L.SIGNATURES)
 
 
+def test_binding_constants_match_the_header():
+    """The Python binding repeats a few #define values of include/cusadi.h; a
+    change on one side only would make the binding's size checks use the
+    wrong limits."""
+    src = open(os.path.join(ROOT, "include", "cusadi.h")).read()
+    m = re.search(r"#define CUSADI_NOALLOC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", src)
+    assert m and int(m.group(1)) << int(m.group(2)) == L.CUSADI_NOALLOC_SCRATCH_BYTES
+    for name in ("CUSADI_ADJ_ACCUMULATE", "CUSADI_ADJ_REDUCE_BROADCAST",
+                 "CUSADI_ADJ_ACCUMULATE_BROADCAST", "CUSADI_BATCH_PERSISTENT", "CUSADI_BATCH_PLAIN"):
+        m = re.search(rf"#define {name} (\d+)u?\b", src)
+        assert m and int(m.group(1)) == getattr(L, name), name
+
+
 def test_default_options():
     o = L.cusadi_default_options()
     assert (o.dtype, o.path, o.block, o.fmad, o.schedule) == (0, 0, 128, 1, 1)
@@ -164,6 +177,28 @@ def test_eval_argument_errors_are_caught_on_the_host():
             L.cusadi_eval(fn, 8, 8, 8, 16, 16, 0, 0)   # ld_in < N
         with pytest.raises(L.CusadiError):
             L.cusadi_adjoint(fn, 8, 16, 8, 16, 8, 16, 16, 8, 0, 0)  # unknown flag
+    finally:
+        L.cusadi_free(fn)
+
+
+def test_sum_and_shared_adjoint_argument_errors_are_caught_on_the_host():
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.addressof(buf)
+    for args in [(7, p, 4, 1, 4, p), (L.CUSADI_F64, p, 2, 1, 4, p), (L.CUSADI_F64, p, 4, 1, 4, 0),
+                 (L.CUSADI_F64, 0, 4, 1, 4, p), (L.CUSADI_F64, p, 4, -1, 4, p),
+                 (L.CUSADI_F64, p, 4, 70000, 4, p)]:
+        with pytest.raises(L.CusadiError) as e:
+            L.cusadi_sum_instances(*args, False, 0)
+        assert e.value.status == L.CUSADI_E_INVALID_ARG
+    L.cusadi_sum_instances(L.CUSADI_F64, p, 4, 0, 4, p, False, 0)     # no rows: nothing to do
+    fn = L.cusadi_load(programs.listing2().to_bytes(), None)
+    try:
+        with pytest.raises(L.CusadiError) as e:
+            L.cusadi_adjoint_shared(fn, p, 4, p, 4, p, 4, 0, 4, 0, 0, 0)
+        assert e.value.status == L.CUSADI_E_INVALID_ARG and "shared_bar" in str(e.value)
+        with pytest.raises(L.CusadiError) as e:
+            L.cusadi_adjoint_shared(fn, p, 4, p, 4, p, 4, p, 4, L.CUSADI_ADJ_REDUCE_BROADCAST, 0, 0)
+        assert e.value.status == L.CUSADI_E_INVALID_ARG
     finally:
         L.cusadi_free(fn)
 

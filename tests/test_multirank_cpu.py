@@ -91,3 +91,90 @@ def test_two_gloo_ranks_match_single_process():
     ybar = rng.standard_normal((13, 257))
     ref = Oracle(programs.srb_step().to_bytes()).adjoint(X, ybar)[:144].sum(axis=1)
     np.testing.assert_allclose(g, ref, rtol=1e-12, atol=1e-12)
+
+
+def _rollout_worker(rank, world, port, out):
+    """Each rank rolls out its own instances through the rollout's autograd
+    function with a CPU step program (the oracle stands in for the library's
+    kernels); the shared gain's gradient must come back summed over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    from oracle import Oracle
+    from paper_2408_09662_gb300 import programs
+    from paper_2408_09662_gb300.rollout import StepProgram, rollout
+    from paper_2408_09662_gb300.shard import instance_range
+
+    class OracleStep(StepProgram):
+        def __init__(self):
+            self.orc = Oracle(programs.srb_step().to_bytes())
+            self.P, self.n = 144, 12
+
+        @property
+        def dtype(self):
+            return torch.float64
+
+        def step(self, src, dst):
+            dst[self.P:] = torch.from_numpy(self.orc.eval(src.numpy()))
+
+        def adjoint_step(self, state, src_bar, dst_bar, shared_bar):
+            xb = self.orc.adjoint(state.numpy(), src_bar[self.P:].numpy())
+            dst_bar[self.P:] = torch.from_numpy(xb[self.P:])
+            shared_bar[:self.P] += torch.from_numpy(xb[:self.P].sum(axis=1))
+
+        def loss_sum(self, buf, out=None):
+            return buf[self.P + self.n].sum()
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(7)
+        N = 37
+        x0 = rng.uniform(-0.1, 0.1, (12, N))
+        K = rng.normal(0.0, 0.1, 144)
+        a, b = instance_range(N, rank, world)
+        xt = torch.tensor(x0[:, a:b], requires_grad=True)
+        kt = torch.tensor(K, requires_grad=True)
+        L, _ = rollout(OracleStep(), xt, kt, 6, checkpoint_every=4)
+        L.backward()
+        out.put((rank, a, b, float(L), xt.grad.numpy(), kt.grad.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_rollout_gradient_of_the_shared_gain_is_summed_over_ranks():
+    from oracle import Oracle
+    from paper_2408_09662_gb300 import programs
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rollout_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # single process, whole batch: the oracle's forward steps and reverse sweeps
+    rng = np.random.default_rng(7)
+    N = 37
+    x0 = rng.uniform(-0.1, 0.1, (12, N))
+    K = rng.normal(0.0, 0.1, 144)
+    orc = Oracle(programs.srb_step().to_bytes())
+    X = np.vstack([np.tile(K[:, None], (1, N)), x0, np.zeros((1, N))])
+    states = []
+    for _ in range(6):
+        states.append(X.copy())
+        X[144:] = orc.eval(X)
+    ybar = np.zeros((13, N))
+    ybar[12] = 1.0
+    gK = np.zeros(144)
+    for S in reversed(states):
+        xb = orc.adjoint(S, ybar)
+        gK += xb[:144].sum(axis=1)
+        ybar = xb[144:]
+    for rank, a, b, L, gx, gk in res:
+        np.testing.assert_allclose(gk, gK, rtol=1e-12, atol=1e-14)      # summed over both ranks
+        np.testing.assert_allclose(gx, ybar[:12, a:b], rtol=1e-12, atol=1e-14)
+        assert abs(L - X[156, a:b].sum()) <= 1e-12 * abs(L)

@@ -428,3 +428,64 @@ def test_mixed_emulation_is_bit_exact_step_by_step():
     # tagging everything, changes the bits
     assert np.any(orc.eval(x, mode=MODE_F32) != y)
     assert np.any(orc.eval(x, mode=MODE_F64).astype(np.float32).astype(np.float64) != y)
+
+
+# ---------------------------------------------------------------------------
+# Monte Carlo arithmetic (Parker 1997): randomly perturbed FP64 evaluations
+# ---------------------------------------------------------------------------
+def test_mca_runs_are_reproducible_and_differ_between_seeds():
+    orc = Oracle(programs.random_program(500, n_in=8, n_out=4, seed=51).to_bytes())
+    x = inputs.normal(8, 64, seed=52)
+    a, b, c = (orc.eval_perturbed(x, kind=1, seed=s) for s in (3, 3, 4))
+    np.testing.assert_array_equal(a, b)
+    assert np.all(a != c)
+    assert np.all(a != orc.eval(x))
+
+
+def test_mca_on_summation_stays_within_the_closed_form_bound():
+    """Each run perturbs every term, partial sum and the stored result by at
+    most u times its size; to first order (exact up to O(u^2) here) its
+    deviation is at most the recursive summation bound plus u |s_k|."""
+    k, N = 40, 256
+    x = inputs.uniform(k, N, 0.5, 2.0, seed=53)
+    orc = Oracle(_chain(Op.ADD, k))
+    y = orc.eval(x)[0]
+    partial = np.cumsum(x, axis=0)
+    bound = _U24 * (x.sum(axis=0) + partial[1:].sum(axis=0) + np.abs(y))
+    for seed in range(4):
+        dev = np.abs(orc.eval_perturbed(x, kind=1, seed=seed)[0] - y)
+        assert np.all(dev <= bound * (1 + 1e-6))
+    with pytest.raises(OracleError):
+        orc.eval_perturbed(x, kind=0)
+
+
+def test_mca_variance_on_summation_is_the_closed_form():
+    """Summation of fixed positive terms: the deviation of a run is, to first
+    order, u * (sum_j x_j xi_j + sum_{j>=2} s_j xi'_j + s_k xi'') with all xi
+    independent and uniform on [-1, 1), so its variance is
+    u^2 (sum x_j^2 + sum s_j^2 + s_k^2) / 3.  Every instance draws its own xi,
+    so identical columns give independent samples; 8,192 of them pin the
+    variance to a few percent."""
+    k, N = 24, 8192
+    col = inputs.uniform(k, 1, 0.5, 2.0, seed=54)
+    x = np.repeat(col, N, axis=1)
+    orc = Oracle(_chain(Op.ADD, k))
+    dev = orc.eval_perturbed(x, kind=1, seed=8)[0] - orc.eval(x)[0]
+    partial = np.cumsum(col[:, 0])
+    var = _U24 ** 2 * (np.sum(col[:, 0] ** 2) + np.sum(partial[1:] ** 2) + partial[-1] ** 2) / 3
+    assert abs(np.var(dev) / var - 1) < 0.08, np.var(dev) / var
+    assert abs(np.mean(dev)) < 5 * np.sqrt(var / N)
+
+
+def test_mca_tolerance_covers_fp32_evaluation_of_a_deep_program():
+    """20,000 generated ops: many outputs keep no correct float digit, where the
+    first-order bound stops being a bound.  The oracle's own FP32 emulation (a
+    correct FP32 evaluation) must still sit within the Monte Carlo rule."""
+    from oracle import tolerance
+    ir = programs.random_program(20000, seed=103).to_bytes()
+    orc = Oracle(ir)
+    x = inputs.normal(64, 32, seed=203).astype(np.float32).astype(np.float64)
+    ref = orc.eval(x)
+    err = np.abs(orc.eval(x, mode=MODE_F32) - ref)
+    tol = tolerance(orc, x, ref, 2e-4, kind=1, mca_runs=8)
+    assert np.all(err <= tol)

@@ -1,12 +1,15 @@
-"""cusadi_eval_noalloc: evaluation for callers that may not allocate device
-memory (a control loop under a no-allocation rule, or code inside a CUDA
-stream capture).  Its workspace is the library's static scratch array.
+"""cusadi_eval_noalloc: evaluation for callers that cannot allocate device
+memory once they run (a real-time control loop under a no-allocation rule, a
+plugin whose host application owns all device memory).  Its workspace is the
+library's static scratch array.
 
-The program here is split into several kernels, so the live values between
-them really go through that scratch array.  Two calls in a row must match
-cusadi_eval on the same inputs within the FP64 parity tolerance of the other
-GPU tests (1e-12 relative to each output row's magnitude).  This file is named
-so that pytest collects it last.
+Two programs exercise both layouts of that workspace: a random program split
+into several compiled kernels, whose carried values go through the array, and
+an LDL^T solve on the interpreter path with more work slots than shared memory
+holds, whose work vector lives in the array ([slots x round_up(N, 128)]).  Two
+calls in a row must match cusadi_eval on the same inputs within the FP64 parity
+tolerance of the other GPU tests (1e-12 relative to each output row's
+magnitude).  This file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -51,3 +54,23 @@ def test_noalloc_rejects_batches_beyond_the_scratch_size():
         L.cusadi_eval_noalloc(fn.handle, x.data_ptr(), N, y.data_ptr(), N, N,
                               torch.cuda.current_stream().cuda_stream)
     assert e.value.status == L.CUSADI_E_INVALID_ARG and "scratch" in str(e.value)
+
+
+def test_noalloc_interpreter_with_work_slots_in_the_scratch():
+    from paper_2408_09662_gb300.experiments import _spd
+    fn = Function(programs.ldlt_spd_solve(47), dtype="f64", path="interp")
+    assert not fn.compiled and fn.info.n_slots * 32 * 8 > 200 * 1024   # too large for shared memory
+    N = 4099
+    assert 0 < L.cusadi_workspace_bytes(fn.handle, N, False) <= L.CUSADI_NOALLOC_SCRATCH_BYTES
+    x = torch.tensor(_spd(47, N, seed=47), device="cuda")
+    ref = fn(x)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        y = torch.full_like(ref, float("nan"))
+        L.cusadi_eval_noalloc(fn.handle, x.data_ptr(), x.stride(0), y.data_ptr(), y.stride(0), N,
+                              stream)
+        torch.cuda.synchronize()
+        r, a = ref.cpu().numpy(), y.cpu().numpy()
+        tol = 1e-12 * np.max(np.abs(r), axis=1, keepdims=True)
+        assert np.all(np.abs(a - r) <= tol), f"call {call}"
