@@ -87,12 +87,26 @@ typedef struct {
                                  program across a group of 32 instances (small batches,
                                  few-instance long programs; at large batches it can also
                                  win: time it); 0: one instance per thread          (0) */
-  int32_t own_math;           /* 1: FP32 sin/cos/exp use the engine's own inline
-                                 implementations (<= 2 ulp; measured slower than the
-                                 library's on the random 20k-op program), 0: library (0) */
+  int32_t own_math;           /* FP32 sin/cos/exp: 0 the library's (out-of-line calls),
+                                 1 the engine's own (<= 2 ulp) inlined, 2 the engine's
+                                 own as out-of-line functions                      (0) */
   int32_t debug_checks;       /* 1: compiled kernels count every non-finite value they
                                  store (NaN, +-inf) in a device counter that
                                  cusadi_debug_count reads; 0: no checks            (0) */
+  int32_t inst_per_thread;    /* 1, 2 or 4: consecutive instances evaluated by each thread
+                                 of the one-thread-per-instance kernels (ways = 0), op by
+                                 op in turn (more independent work per thread, more
+                                 registers); their inputs and outputs move as one
+                                 float2/float4/double2 access when the buffers allow it
+                                 (16-byte aligned base, ld a multiple of it)         (1) */
+  int32_t coop_groups;        /* 1..8: groups of 32 instances per CTA of the cooperative
+                                 kernels (ways > 1): 32 * ways * coop_groups threads
+                                 per CTA; warps of one role in one CTA run the same
+                                 code together                                      (1) */
+  int32_t sync_every;         /* one-thread-per-instance kernels: a CTA-wide barrier
+                                 after every this many ops, so the CTA's warps stay in
+                                 the same stretch of a long kernel's code (instruction
+                                 cache reuse); 0: no barriers                       (0) */
   const char* cache_dir;      /* directory for compiled kernels, NULL = in-memory only */
 } cusadi_options;
 

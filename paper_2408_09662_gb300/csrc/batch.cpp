@@ -349,7 +349,7 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
       co.dtype = o.dtype;
       co.segment_ops = o.segment_ops;
       co.inline_math = o.inline_math != 0;
-      co.own_math = o.own_math != 0;
+      co.own_math = o.own_math;
       co.device_fn = true;
       co.prefix = "cs_b" + std::to_string(p);
       // a cooperative program is linked in cooperative form only

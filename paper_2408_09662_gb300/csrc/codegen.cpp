@@ -153,6 +153,56 @@ static __device__ __forceinline__ float cs_own_exp_f(float x) {
 }
 )";
 
+// Own math as generated: mode 1 inlines sin/cos/exp at every use, mode 2 makes
+// them out-of-line functions (one copy of the code, a call per use).
+std::string own_math_source(int mode) {
+  std::string t = kOwnMathF32;
+  if (mode == 2) {
+    const std::string a = "__forceinline__ float cs_own_", b = "__noinline__ float cs_own_";
+    for (size_t p = t.find(a); p != std::string::npos; p = t.find(a, p + b.size())) t.replace(p, a.size(), b);
+  }
+  return t;
+}
+
+// Accesses of NL consecutive instances of one row by one thread (NL = 2 or 4):
+// one vector load/store when `full` (the caller checked alignment and that all
+// NL instances are inside the batch), else one element at a time, the lanes
+// past the batch's end reading lane 0's element and storing nothing.
+const char* kLaneAccess = R"(template <typename T> struct cs_vec2;
+template <> struct cs_vec2<float> { typedef float2 t; };
+template <> struct cs_vec2<double> { typedef double2 t; };
+template <typename T>
+static __device__ __forceinline__ void cs_ld2(const T* __restrict__ p, bool full, int m, T& a, T& b) {
+  if (full) { const typename cs_vec2<T>::t v = *reinterpret_cast<const typename cs_vec2<T>::t*>(p); a = v.x; b = v.y; }
+  else { a = p[0]; b = m > 1 ? p[1] : a; }
+}
+template <typename T>
+static __device__ __forceinline__ void cs_st2(T* __restrict__ p, bool full, int m, T a, T b) {
+  if (full) { typename cs_vec2<T>::t v; v.x = a; v.y = b; *reinterpret_cast<typename cs_vec2<T>::t*>(p) = v; }
+  else { p[0] = a; if (m > 1) p[1] = b; }
+}
+static __device__ __forceinline__ void cs_ld4(const float* __restrict__ p, bool full, int m, float& a, float& b,
+                                              float& c, float& d) {
+  if (full) { const float4 v = *reinterpret_cast<const float4*>(p); a = v.x; b = v.y; c = v.z; d = v.w; }
+  else { a = p[0]; b = m > 1 ? p[1] : a; c = m > 2 ? p[2] : a; d = m > 3 ? p[3] : a; }
+}
+static __device__ __forceinline__ void cs_st4(float* __restrict__ p, bool full, int m, float a, float b, float c,
+                                              float d) {
+  if (full) *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+  else { p[0] = a; if (m > 1) p[1] = b; if (m > 2) p[2] = c; if (m > 3) p[3] = d; }
+}
+static __device__ __forceinline__ void cs_ld4(const double* __restrict__ p, bool full, int m, double& a, double& b,
+                                              double& c, double& d) {
+  if (full) { cs_ld2(p, true, 2, a, b); cs_ld2(p + 2, true, 2, c, d); }
+  else { a = p[0]; b = m > 1 ? p[1] : a; c = m > 2 ? p[2] : a; d = m > 3 ? p[3] : a; }
+}
+static __device__ __forceinline__ void cs_st4(double* __restrict__ p, bool full, int m, double a, double b,
+                                              double c, double d) {
+  if (full) { cs_st2(p, true, 2, a, b); cs_st2(p + 2, true, 2, c, d); }
+  else { p[0] = a; if (m > 1) p[1] = b; if (m > 2) p[2] = c; if (m > 3) p[3] = d; }
+}
+)";
+
 // C expression of one op with operand expressions A, B in precision f.
 std::string op_expr(Gen& G, const Node& x, bool f, const std::string& A, const std::string& B,
                     const CodegenOptions& o) {
@@ -265,82 +315,154 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
 
   const char* tin = G.buf_f64() ? "double" : "float";
   const char* tw = G.ws_f64() ? "double" : "float";
+  // Lanes: a kernel thread evaluates NL consecutive instances i .. i + NL - 1,
+  // op by op in turn; their inputs and outputs move as one vector access when
+  // the buffers allow it.  A kernel thread past the end of the batch still runs
+  // (CTA barriers need it) on the last thread's instances, storing nothing.
+  const int NL = o.device_fn ? 1 : std::max(1, o.inst_per_thread);
+  const bool clamped = o.adjoint || NL > 1 || (o.sync_every > 0 && !o.device_fn);
+  R.inst_per_thread = NL;
+  auto vname = [&](int64_t i, int r) {
+    return NL == 1 ? "v" + std::to_string(i) : "v" + std::to_string(i) + "_" + std::to_string(r);
+  };
+  // a comma-separated list of the NL lane names of node i
+  auto lanes = [&](int64_t i) {
+    std::string l;
+    for (int r = 0; r < NL; ++r) l += (r ? ", " : "") + vname(i, r);
+    return l;
+  };
 
   for (int s = 0; s < nseg; ++s) {
     std::ostringstream body;
     std::vector<uint8_t> have(n, 0);   // leaf or ws value materialised in this segment
+    std::vector<uint8_t> decl_buf(n, 0);  // lanes declared with the buffer's type, not the op's
     G.calls.clear();
     G.own_f32 = false;
-    auto operand = [&](int32_t i, bool want_f64) -> std::string {
+    auto operand = [&](int32_t i, bool want_f64, int r) -> std::string {
       const Node& x = g.nodes[i];
       bool f = G.node_f64(i);
-      std::string name = "v" + std::to_string(i);
       if (x.op == CONST) return lit(x.k, want_f64);
       if (x.op == INPUT) {
         if (!have[i]) {
           have[i] = 1;
           const bool second = o.split >= 0 && x.io >= o.split;
           const int64_t row = second ? x.io - o.split : x.io;
-          body << "  const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")"
-               << (second ? (x.bcast ? "X2b[" : "X2[") : (x.bcast ? "Xb[" : "X[")) << row
-               << (second ? "ll * ldx2];\n" : "ll * ldx];\n");
+          const std::string src = std::string(second ? (x.bcast ? "X2b[" : "X2[") : (x.bcast ? "Xb[" : "X[")) +
+                                  std::to_string(row) + (second ? "ll * ldx2]" : "ll * ldx]");
+          if (NL == 1 || x.bcast) {
+            // a broadcast row holds one value for every instance: all lanes share it
+            body << "  const " << G.ty(f) << " v" << i << " = (" << G.ty(f) << ")" << src << ";\n";
+          } else {
+            decl_buf[i] = 1;
+            body << "  " << tin << " " << lanes(i) << ";\n"
+                 << "  cs_ld" << NL << "(&" << src << ", full, m, " << lanes(i) << ");\n";
+          }
         }
-      } else if (G.seg_of[i] != s) {
+        std::string name = (NL == 1 || x.bcast) ? "v" + std::to_string(i) : vname(i, r);
+        const bool df = decl_buf[i] ? G.buf_f64() : f;
+        if (df != want_f64) return std::string("(") + G.ty(want_f64) + ")" + name;
+        return name;
+      }
+      if (G.seg_of[i] != s) {
         if (!have[i]) {
           have[i] = 1;
-          body << "  const " << G.ty(f) << " " << name << " = (" << G.ty(f) << ")W["
-               << G.ws_slot[i] << "ll * ldw];\n";
+          if (NL == 1) {
+            body << "  const " << G.ty(f) << " v" << i << " = (" << G.ty(f) << ")W["
+                 << G.ws_slot[i] << "ll * ldw];\n";
+          } else {
+            decl_buf[i] = 1;   // workspace columns are padded to 32: always whole vectors
+            body << "  " << tw << " " << lanes(i) << ";\n"
+                 << "  cs_ld" << NL << "(&W[" << G.ws_slot[i] << "ll * ldw], true, " << NL << ", "
+                 << lanes(i) << ");\n";
+          }
         }
       }
-      if (f != want_f64) return std::string("(") + G.ty(want_f64) + ")" + name;
-      return name;
+      const bool df = decl_buf[i] ? G.ws_f64() : f;
+      if (df != want_f64) return std::string("(") + G.ty(want_f64) + ")" + vname(i, r);
+      return vname(i, r);
     };
-    auto store_out = [&](int64_t r, const std::string& v) {
+    // stores of output row r of node i (values v[lane])
+    auto store_out = [&](int64_t r, const std::vector<std::string>& v) {
       if (o.adjoint) {
-        if (g.out_reduce[r]) {
-          // the instance's term goes to the workspace (a coalesced store); the
-          // finishing kernel sums each such row over the instances
-          body << "  if (reduce) {\n    if (active) Wp[" << reduce_k[r] << "ll * ldw] = (" << tw << ")" << v
-               << ";\n"
-               << "  } else if (active) { " << tin << "* p_ = &Y[" << r << "ll * ldy]; *p_ = acc ? *p_ + ("
-               << tin << ")" << v << " : (" << tin << ")" << v << "; }\n";
-        } else {
-          body << "  if (active) { " << tin << "* p_ = &Y[" << r << "ll * ldy]; *p_ = acc ? *p_ + ("
-               << tin << ")" << v << " : (" << tin << ")" << v << "; }\n";
+        for (int l = 0; l < NL; ++l) {
+          const std::string guard = NL == 1 ? "active" : "active && m > " + std::to_string(l);
+          const std::string off = NL == 1 ? "" : " + " + std::to_string(l);
+          const std::string plain = "if (" + guard + ") { " + tin + "* p_ = &Y[" + std::to_string(r) +
+                                    "ll * ldy" + off + "]; *p_ = acc ? *p_ + (" + tin + ")" + v[l] + " : (" +
+                                    tin + ")" + v[l] + "; }";
+          if (g.out_reduce[r]) {
+            // the instance's term goes to the workspace (a coalesced store); the
+            // finishing kernel sums each such row over the instances
+            body << "  if (reduce) {\n    if (" << guard << ") Wp[" << reduce_k[r] << "ll * ldw" << off
+                 << "] = (" << tw << ")" << v[l] << ";\n  } else " << plain << "\n";
+          } else {
+            body << "  " << plain << "\n";
+          }
         }
+      } else if (NL == 1) {
+        body << "  " << (clamped ? "if (active) " : "") << "Y[" << r << "ll * ldy] = (" << tin << ")" << v[0] << ";\n";
       } else {
-        body << "  Y[" << r << "ll * ldy] = (" << tin << ")" << v << ";\n";
+        body << "  if (active) cs_st" << NL << "(&Y[" << r << "ll * ldy], full, m";
+        for (int l = 0; l < NL; ++l) body << ", (" << tin << ")" << v[l];
+        body << ");\n";
       }
       if (o.debug_checks && !o.device_fn)   // count non-finite results (cusadi_debug_count)
-        body << "  if (active && !isfinite((double)(" << v << "))) atomicAdd(&cs_dbg, 1u);\n";
+        for (int l = 0; l < NL; ++l)
+          body << "  if (active" << (NL == 1 ? "" : " && m > " + std::to_string(l)) << " && !isfinite((double)("
+               << v[l] << "))) atomicAdd(&cs_dbg, 1u);\n";
+    };
+    auto lane_values = [&](int64_t i, bool f) {
+      std::vector<std::string> v;
+      for (int l = 0; l < NL; ++l) v.push_back(G.leaf(i) ? operand((int32_t)i, f, l) : vname(i, l));
+      return v;
     };
     // outputs fed directly by inputs or constants are written by segment 0
     if (s == 0) {
       for (int64_t i = 0; i < n; ++i) {
         if (!G.leaf(i) || G.out_rows[i].empty()) continue;
-        std::string v = operand((int32_t)i, G.node_f64((int32_t)i));
+        std::vector<std::string> v = lane_values(i, G.node_f64((int32_t)i));
         for (int64_t r : G.out_rows[i]) store_out(r, v);
       }
     }
+    int64_t since_sync = 0;
     for (int64_t i = segs[s].first; i < segs[s].second; ++i) {
       if (G.leaf(i)) continue;
       const Node& x = g.nodes[i];
       const bool f = G.node_f64((int32_t)i);
       const char* T = G.ty(f);
-      std::string A = x.a >= 0 ? operand(x.a, f) : "";
-      std::string B = x.b >= 0 ? operand(x.b, f) : "";
-      std::string e = op_expr(G, x, f, A, B, o);
-      body << "  const " << T << " v" << i << " = " << e << ";\n";
-      if (G.ws_slot[i] >= 0)
-        body << "  if (active) W[" << G.ws_slot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
-      for (int64_t r : G.out_rows[i]) store_out(r, "v" + std::to_string(i));
+      for (int l = 0; l < NL; ++l) {
+        std::string A = x.a >= 0 ? operand(x.a, f, l) : "";
+        std::string B = x.b >= 0 ? operand(x.b, f, l) : "";
+        body << "  const " << T << " " << vname(i, l) << " = " << op_expr(G, x, f, A, B, o) << ";\n";
+      }
+      if (G.ws_slot[i] >= 0) {
+        if (NL == 1) {
+          body << "  if (active) W[" << G.ws_slot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
+        } else {
+          body << "  if (active) cs_st" << NL << "(&W[" << G.ws_slot[i] << "ll * ldw], true, " << NL;
+          for (int l = 0; l < NL; ++l) body << ", (" << tw << ")" << vname(i, l);
+          body << ");\n";
+        }
+      }
+      if (!G.out_rows[i].empty()) {
+        std::vector<std::string> v = lane_values(i, f);
+        for (int64_t r : G.out_rows[i]) store_out(r, v);
+      }
+      if (o.sync_every > 0 && !o.device_fn && ++since_sync >= o.sync_every) {
+        body << "  __syncthreads();\n";
+        since_sync = 0;
+      }
     }
 
     std::ostringstream src;
     src << "// Generated straight-line kernel: segment " << s << " of " << nseg
         << (o.adjoint ? " (adjoint)" : "") << ", dtype "
-        << (o.dtype == CUSADI_F64 ? "f64" : (o.dtype == CUSADI_F32 ? "f32" : "mixed")) << "\n";
-    if (G.own_f32) src << kOwnMathF32;
+        << (o.dtype == CUSADI_F64 ? "f64" : (o.dtype == CUSADI_F32 ? "f32" : "mixed"));
+    if (NL > 1) src << ", " << NL << " instances per thread";
+    if (o.sync_every > 0 && !o.device_fn) src << ", CTA barrier every " << o.sync_every << " ops";
+    src << "\n";
+    if (NL > 1) src << kLaneAccess;
+    if (G.own_f32) src << own_math_source(o.own_math);
     if (o.debug_checks && !o.device_fn) src << "__device__ unsigned int cs_dbg;   // non-finite results\n";
     if (!o.inline_math) {
       for (auto& c : G.calls) {
@@ -379,13 +501,22 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
         << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
         << "* __restrict__ X2, long long ldx2, " << tin
         << "* __restrict__ Y, long long ldy,\n    long long N, " << tw
-        << "* __restrict__ W, long long ldw, int acc, int reduce) {\n"
-        << "  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n";
-    if (o.adjoint) {
-      src << "  const bool active = i0 < N;\n"
-          << "  const long long i = active ? i0 : N - 1;\n";
+        << "* __restrict__ W, long long ldw, int acc, int reduce, int vec) {\n";
+    if (NL == 1) {
+      src << "  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n";
+      if (clamped) {
+        src << "  const bool active = i0 < N;\n"
+            << "  const long long i = active ? i0 : N - 1;\n";
+      } else {
+        src << "  if (i0 >= N) return;\n  const bool active = true;\n  const long long i = i0;\n";
+      }
     } else {
-      src << "  if (i0 >= N) return;\n  const bool active = true;\n  const long long i = i0;\n";
+      // m: instances of this thread inside the batch; full: whole vector accesses
+      src << "  const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * " << NL << ";\n"
+          << "  const bool active = i0 < N;\n"
+          << "  const long long i = active ? i0 : (N - 1) / " << NL << " * " << NL << ";\n"
+          << "  const int m = N - i < " << NL << " ? (int)(N - i) : " << NL << ";\n"
+          << "  const bool full = vec != 0 && m == " << NL << ";\n";
     }
     src << "  const " << tin << "* __restrict__ Xb = X;\n"
         << "  const " << tin << "* __restrict__ X2b = X2;\n"
@@ -393,7 +524,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     if (o.adjoint && R.has_reduce)
       src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw + i;  // reduced-row terms\n";
     src << "  X += i; X2 += i; Y += i; W += i;\n"
-        << "  (void)Xb; (void)X2b; (void)Yb; (void)W; (void)ldw; (void)ldx2; (void)acc; (void)reduce; (void)active;\n"
+        << "  (void)Xb; (void)X2b; (void)Yb; (void)W; (void)ldw; (void)ldx2; (void)acc; (void)reduce; (void)active; (void)vec;\n"
         << body.str() << "}\n";
     Segment S;
     S.begin = segs[s].first;
@@ -456,6 +587,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
   Gen G(g, o);
   const int64_t n = (int64_t)g.nodes.size();
   const int W = plan.ways;
+  const int NG = o.device_fn ? 1 : std::max(1, o.coop_groups);   // groups of 32 instances per CTA
   G.out_rows.assign(n, {});
   for (size_t r = 0; r < g.out.size(); ++r) G.out_rows[g.out[r]].push_back((int64_t)r);
   // segments: runs of whole phases of at most ~segment_ops ops
@@ -668,7 +800,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     std::ostringstream src;
     src << "// Generated cooperative kernel: segment " << s << " of " << nseg << ", " << W
         << " warps per 32 instances, " << (segs[s].second - segs[s].first) << " phases\n";
-    if (G.own_f32) src << kOwnMathF32;
+    if (G.own_f32) src << own_math_source(o.own_math);
     if (o.debug_checks && !o.device_fn) src << "__device__ unsigned int cs_dbg;   // non-finite results\n";
     if (!o.inline_math) {
       for (auto& c : G.calls) {
@@ -707,21 +839,25 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
       R.segs.push_back(std::move(S));
       continue;
     }
-    src << "extern \"C\" __global__ void __launch_bounds__(" << 32 * W << ") " << name << "(\n"
+    // NG groups of 32 instances per CTA: warp w of every group runs role w % W
+    // on group w / W, each group with its own block of shared slots
+    src << "extern \"C\" __global__ void __launch_bounds__(" << 32 * W * NG << ") " << name << "(\n"
         << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
         << "* __restrict__ X2, long long ldx2, " << tin << "* __restrict__ Y, long long ldy,\n    long long N, "
-        << tw << "* __restrict__ W, long long ldw, int acc, int reduce) {\n"
+        << tw << "* __restrict__ W, long long ldw, int acc, int reduce, int vec) {\n"
         << "  extern __shared__ __align__(16) unsigned char cs_smem[];\n"
-        << "  " << tsm << "* __restrict__ cs_x = reinterpret_cast<" << tsm << "*>(cs_smem);\n"
-        << "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n"
-        << "  const long long i0 = (long long)blockIdx.x * 32 + lane;\n"
+        << "  const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) % " << W
+        << ", grp = (threadIdx.x >> 5) / " << W << ";\n"
+        << "  " << tsm << "* __restrict__ cs_x = reinterpret_cast<" << tsm << "*>(cs_smem) + grp * "
+        << std::max(n_slots, 1) * 32 << ";\n"
+        << "  const long long i0 = ((long long)blockIdx.x * " << NG << " + grp) * 32 + lane;\n"
         << "  const bool active = i0 < N;\n"
         << "  const long long i = active ? i0 : N - 1;\n"
         << "  const " << tin << "* __restrict__ Xb = X;\n"
         << "  const " << tin << "* __restrict__ X2b = X2;\n";
     if (R.has_reduce) src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw + i;  // reduced-row terms\n";
     src << "  X += i; X2 += i; Y += i; W += i;\n"
-        << "  (void)Xb; (void)X2b; (void)ldx2; (void)W; (void)ldw; (void)acc; (void)reduce; (void)cs_x;\n"
+        << "  (void)Xb; (void)X2b; (void)ldx2; (void)W; (void)ldw; (void)acc; (void)reduce; (void)cs_x; (void)vec;\n"
         << regions.str() << "}\n";
     Segment S;
     S.begin = segs[s].first;
@@ -731,7 +867,8 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     R.segs.push_back(std::move(S));
   }
   R.coop_ways = W;
-  R.smem_bytes = (int64_t)std::max(n_slots, 1) * 32 * (sm_f64 ? 8 : 4);
+  R.coop_groups = NG;
+  R.smem_bytes = (int64_t)NG * std::max(n_slots, 1) * 32 * (sm_f64 ? 8 : 4);
   if (R.has_reduce && !o.device_fn) R.segs[0].source += finish_source(R, o.prefix, tin, tw);
   return R;
 }

@@ -97,7 +97,9 @@ struct CodegenResult {
   // terms in a fixed order
   std::vector<int64_t> reduce_rows;
   std::string finish_kernel;
-  int coop_ways = 0;             // > 0: cooperative kernels, 32 * coop_ways threads per CTA
+  int coop_ways = 0;             // > 0: cooperative kernels, 32 * coop_ways threads per group
+  int coop_groups = 1;           // groups of 32 instances per CTA (cooperative kernels)
+  int inst_per_thread = 1;       // consecutive instances per thread (one-thread kernels)
   int64_t smem_bytes = 0;        // dynamic shared memory per CTA (cooperative kernels)
 };
 
@@ -106,7 +108,11 @@ struct CodegenOptions {
   int block = 128;
   int64_t segment_ops = 40000;
   bool inline_math = false;
-  bool own_math = false;         // own FP32 sin/cos/exp instead of library calls
+  int own_math = 0;              // own FP32 sin/cos/exp instead of library calls:
+                                 // 1 inlined, 2 out-of-line functions
+  int inst_per_thread = 1;       // one-thread kernels: R consecutive instances per thread
+  int sync_every = 0;            // one-thread kernels: a CTA barrier every this many ops
+  int coop_groups = 1;           // cooperative kernels: groups of 32 instances per CTA
   bool adjoint = false;
   int64_t split = -1;            // input rows >= split come from the second buffer
   bool device_fn = false;        // emit relocatable __device__ functions of one instance

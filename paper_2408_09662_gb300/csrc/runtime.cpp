@@ -217,8 +217,11 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.block = fn->opt.block;
   co.segment_ops = fn->opt.segment_ops;
   co.inline_math = fn->opt.inline_math != 0;
-  co.own_math = fn->opt.own_math != 0;
+  co.own_math = fn->opt.own_math;
   co.debug_checks = fn->opt.debug_checks != 0;
+  co.inst_per_thread = fn->opt.ways > 1 ? 1 : fn->opt.inst_per_thread;
+  co.sync_every = fn->opt.ways > 1 ? 0 : fn->opt.sync_every;
+  co.coop_groups = fn->opt.coop_groups;
   co.adjoint = adjoint;
   co.split = adjoint ? fn->ir.nnz_in : -1;
   static const char* tag[] = {"f64", "f32", "mixed"};
@@ -227,6 +230,8 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
     co.prefix = std::string(adjoint ? "cs_coopadj" : "cs_coop") + std::to_string(fn->opt.ways) + "_" +
                 tag[fn->opt.dtype];
     CoopPlan plan = plan_coop(d.g, fn->opt.ways, 8.0);
+    // the CTA's groups share the shared-memory budget
+    co.coop_shared_kb = std::min(co.coop_shared_kb, 200 / std::max(1, co.coop_groups));
     d.cg = generate_coop(d.g, co, plan);
     if (d.cg.smem_bytes > 200 * 1024)   // cannot happen: overflow goes to the workspace
       return fail(CUSADI_E_UNSUPPORTED, "cooperative plan needs too much shared memory");
@@ -412,19 +417,35 @@ cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const 
   // small batches: shrink the CTA (in warps) until every SM gets one, since a
   // straight-line kernel's throughput per SM does not depend on how many CTAs
   // share it but idle SMs are lost (N = 4096 at 128 threads fills 32 of 152)
+  const int64_t NL = std::max(1, d.cg.inst_per_thread);
+  const int64_t threads = (N + NL - 1) / NL;
   unsigned block = (unsigned)fn->opt.block;
-  while (block > 32 && ds.sms > 0 && (N + block - 1) / block < ds.sms) block = (block / 2 + 31) / 32 * 32;
-  unsigned grid = (unsigned)((N + block - 1) / block);
+  if (fn->opt.sync_every <= 0)
+    while (block > 32 && ds.sms > 0 && (threads + block - 1) / block < ds.sms) block = (block / 2 + 31) / 32 * 32;
+  unsigned grid = (unsigned)((threads + block - 1) / block);
   unsigned smem = 0;
-  if (d.cg.coop_ways > 0) {   // W warps per 32 instances
-    block = 32u * (unsigned)d.cg.coop_ways;
-    grid = (unsigned)((N + 31) / 32);
+  if (d.cg.coop_ways > 0) {   // W warps per group of 32 instances, G groups per CTA
+    const int G = std::max(1, d.cg.coop_groups);
+    block = 32u * (unsigned)d.cg.coop_ways * (unsigned)G;
+    grid = (unsigned)((N + 32 * G - 1) / (32 * G));
     smem = (unsigned)d.cg.smem_bytes;
+  }
+  // whole-vector accesses of NL consecutive instances: every buffer a vector
+  // touches starts on a multiple of the vector and its rows are a whole number
+  // of vectors apart
+  int vec = 0;
+  if (NL > 1) {
+    const size_t elt = elt_io(fn->opt.dtype);
+    const size_t a = std::min<size_t>(16, (size_t)NL * elt);
+    auto ok = [&](const void* p, int64_t ld) {
+      return p == nullptr || ((uintptr_t)p % a == 0 && ((size_t)ld * elt) % a == 0);
+    };
+    vec = ok(X, ldx) && ok(X2, ldx2) && ok(Y, ldy) ? 1 : 0;
   }
   long long lx = ldx, lx2 = ldx2, ly = ldy, n = N, lw = ldw > 0 ? ldw : round_up(N, 32);
   const void* x2 = X2 ? X2 : X;
   for (size_t s = 0; s < fs.size(); ++s) {
-    void* args[] = {(void*)&X, &lx, (void*)&x2, &lx2, &Y, &ly, &n, &W, &lw, &acc, &reduce};
+    void* args[] = {(void*)&X, &lx, (void*)&x2, &lx2, &Y, &ly, &n, &W, &lw, &acc, &reduce, &vec};
     CUresult r = driver().launchKernel(fs[s], grid, 1, 1, block, 1, 1, smem, (CUstream)stream, args, nullptr);
     if (r != CUDA_SUCCESS) return cuda_fail("cuLaunchKernel", r);
   }
@@ -497,6 +518,9 @@ void cusadi_default_options(cusadi_options* o) {
   o->own_math = 0;
   o->ways = 0;
   o->debug_checks = 0;
+  o->inst_per_thread = 1;
+  o->coop_groups = 1;
+  o->sync_every = 0;
   o->cache_dir = nullptr;
 }
 
@@ -537,6 +561,15 @@ cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* o
   if (o.maxrregcount < 0 || o.maxrregcount > 255) return fail(CUSADI_E_INVALID_ARG, "maxrregcount must be in [0, 255]");
   if (o.compile_limit_ops <= 0) o.compile_limit_ops = 300000;
   if (o.ways < 0 || o.ways > 16 || o.ways == 1) return fail(CUSADI_E_INVALID_ARG, "ways must be 0 or 2..16");
+  if (o.own_math < 0 || o.own_math > 2) return fail(CUSADI_E_INVALID_ARG, "own_math must be 0, 1 or 2");
+  if (o.inst_per_thread <= 0) o.inst_per_thread = 1;
+  if (o.inst_per_thread != 1 && o.inst_per_thread != 2 && o.inst_per_thread != 4)
+    return fail(CUSADI_E_INVALID_ARG, "inst_per_thread must be 1, 2 or 4");
+  if (o.coop_groups <= 0) o.coop_groups = 1;
+  if (o.coop_groups > 8) return fail(CUSADI_E_INVALID_ARG, "coop_groups must be in 1..8");
+  if (o.ways > 1 && 32 * o.ways * o.coop_groups > 1024)
+    return fail(CUSADI_E_INVALID_ARG, "32 * ways * coop_groups must not exceed 1024 threads");
+  if (o.sync_every < 0) return fail(CUSADI_E_INVALID_ARG, "sync_every must be >= 0");
   if (o.cache_dir) fn->cache_dir = o.cache_dir;
   o.cache_dir = nullptr;  // the caller's string is not kept
   auto t0 = std::chrono::steady_clock::now();

@@ -1,0 +1,140 @@
+"""Autotuner of the compiled path's launch configuration.
+
+CusADi fixes one kernel shape for every function (one instance per thread,
+§III-A, Listing 2).  Which shape is fastest here depends on the program and
+the batch: the register footprint decides how many warps an SM holds, a long
+program with few instances wants several warps per instance group, a short
+one wants more instances per thread, and a megabyte-sized kernel wants its
+warps to stay in the same stretch of code.  The tuner compiles candidate
+configurations (concurrently: the compiles release the GIL), times each on the
+caller's own batch (CUDA events on the current stream, L2 flushed before every
+launch, median of `reps`) and keeps the fastest.  The choice is cached on disk
+keyed by the program's content hash, the GPU, the dtype, the batch size (to
+the next power of two) and the caller's fixed options, so a later call loads
+the chosen kernel directly.
+
+Search, in two rounds:
+1. shape: ways in `ways` (0 = one thread per instance, W = W warps per group
+   of 32 instances);
+2. around the best shape: for ways = 0, instances per thread (2, 4), a CTA
+   barrier every few hundred ops with larger CTAs, and register caps; for
+   ways > 0, 2 or 4 groups of 32 instances per CTA.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import statistics
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+import torch
+
+from .api import DEFAULT_CACHE, Function, _program_bytes
+
+
+def _refinements(best: dict, dtype: str, n_ops: int, n_slots: int) -> list:
+    """Candidate option sets one step away from `best`.  Instances per thread
+    multiply the live values a thread holds, so a count whose values cannot
+    fit in 255 registers (two per FP64 value) is not tried."""
+    out = []
+    if best.get("ways", 0) == 0:
+        regs_per_value = 2 if dtype == "f64" else 1
+        out += [dict(best, inst_per_thread=r) for r in (2, 4) if n_slots * r * regs_per_value <= 255]
+        if n_ops >= 2000:   # long kernels: keep each CTA's warps in the same stretch of code
+            out += [dict(best, block=256, sync_every=256), dict(best, block=512, sync_every=1024)]
+        if n_slots * regs_per_value > 96:   # register-bound occupancy: cap and let the compiler spill
+            out += [dict(best, maxrregcount=128), dict(best, maxrregcount=96)]
+    else:
+        out += [dict(best, coop_groups=2), dict(best, coop_groups=4)]
+    return out
+
+
+def _key(ir: bytes, dtype: str, N: int, fixed: dict, device) -> str:
+    props = torch.cuda.get_device_properties(device)
+    bucket = 1 << max(0, (int(N) - 1).bit_length())
+    h = hashlib.sha256(ir).hexdigest()[:20]
+    fx = ",".join(f"{k}={fixed[k]}" for k in sorted(fixed))
+    return f"{h}|{props.name}|sm_{props.major}{props.minor}|{dtype}|N<={bucket}|{fx}"
+
+
+def _load_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(path: str, key: str, rec: dict) -> None:
+    d = _load_cache(path)
+    d[key] = rec
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    fd, tmp = tempfile.mkstemp(dir=os.path.dirname(path), prefix=".tuning")
+    with os.fdopen(fd, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time(fn: Function, x: torch.Tensor, y: torch.Tensor, flush: torch.Tensor, reps: int) -> float:
+    for _ in range(2):
+        fn(x, out=y)
+    ts = []
+    stream = torch.cuda.current_stream(x.device)
+    for _ in range(reps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn(x, out=y)
+        e.record(stream)
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+    return statistics.median(ts)
+
+
+def autotune(program, x: torch.Tensor, dtype: str = "f64", ways=(0, 2, 4, 8), refine: bool = True,
+             reps: int = 5, flush_bytes: int = 256 << 20, cache_dir=DEFAULT_CACHE,
+             use_cache: bool = True, compile_workers: int = 4, **fixed) -> Function:
+    """The program compiled in the fastest configuration found for the batch x
+    ([nnz_in, N] CUDA tensor of the dtype's element type).  `fixed` options
+    (e.g. fmad=0) apply to every candidate.  The returned Function carries
+    `.tune_record`: the chosen options, their time and every candidate's time
+    (ms), and whether the record came from the cache."""
+    ir = _program_bytes(program)
+    N = int(x.shape[1])
+    key = _key(ir, dtype, N, fixed, x.device)
+    path = os.path.join(cache_dir, "tuning.json") if cache_dir else None
+    if use_cache and path:
+        rec = _load_cache(path).get(key)
+        if rec is not None:
+            fn = Function(ir, dtype=dtype, cache_dir=cache_dir, **fixed, **rec["options"])
+            fn.tune_record = dict(rec, from_cache=True)
+            return fn
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device=x.device)
+    tried = {}          # frozen options -> (ms, Function)
+
+    def build(opts):
+        return Function(ir, dtype=dtype, cache_dir=cache_dir, **fixed, **opts)
+
+    def run_round(cands):
+        cands = [c for c in cands if tuple(sorted(c.items())) not in tried]
+        with ThreadPoolExecutor(max(1, min(compile_workers, len(cands)))) as ex:
+            fns = list(ex.map(build, cands))
+        for c, fn in zip(cands, fns):       # timed one after the other, nothing else on the GPU
+            y = torch.empty((fn.nnz_out, N), dtype=fn.torch_dtype, device=x.device)
+            tried[tuple(sorted(c.items()))] = (_time(fn, x, y, flush, reps), fn)
+
+    run_round([{"ways": int(w)} for w in ways])
+    if refine:
+        best = min(tried, key=lambda k: tried[k][0])
+        info = tried[best][1].info
+        run_round(_refinements(dict(best), dtype, info.n_ops, info.n_slots))
+    best = min(tried, key=lambda k: tried[k][0])
+    ms, fn = tried[best]
+    rec = {"options": dict(best), "ms": ms, "N": N,
+           "candidates": [[dict(k), v[0]] for k, v in sorted(tried.items(), key=lambda kv: kv[1][0])]}
+    if path:
+        _store_cache(path, key, rec)
+    fn.tune_record = dict(rec, from_cache=False)
+    return fn
