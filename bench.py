@@ -34,17 +34,15 @@ N_INST = 65536
 N_OPS_GEN = 20000
 PROGRAM_SEED, INPUT_SEED = 0, 1
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per launch from an ncu capture of the generated
-# kernel with this source hash (profiles/cs_fwd_f64_random20k.md); a kernel
-# whose source changed since gets no traffic figure
 # ALU peaks derived from unit counts and clocks (GB300: 152 SMs, 2070 MHz max SM
 # clock): FP64 1.25 TFLOP/s = 0.625 TFMA/s (about 2 FMA per clock per SM); FP32
 # 128 FMA per clock per SM = 40.3 TFMA/s.  The measured FMA-chain rates of
 # peaks.py are reported beside them.
 NOMINAL_FMA_PER_S = {"f64": 1.25e12 / 2, "f32": 152 * 128 * 2.07e9}
-NCU_TRAFFIC = {"c26c9219142915d9": 26148096 + 463616,   # one thread per instance
-               "95ad52848a2dde30": 26208000 + 11008,    # 2 warps per 32 instances
-               "562155cee3621147": 26315776 + 2560}     # 4 warps per 32 instances
+# DRAM bytes (read + write) per launch that an ncu capture measured for the
+# generated kernel with this source hash; a kernel whose source changed since
+# the capture gets no traffic figure (null) rather than a stale one
+NCU_TRAFFIC = {}
 
 
 def workload_config(info=None):
@@ -205,9 +203,10 @@ def other_configs(dev, pk64, pk32, flush, reps, oracle_check=True):
     def make_batch():
         t0 = time.perf_counter()
         irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(sizes)]
-        # ways=4: programs with few instances and many ops (here the 50k-200k-op
-        # ones) run as cooperative tiles in the 128-thread scheduler
-        return Batch(irs, [N for _, N in sizes], dtype="f32", ways=4), time.perf_counter() - t0, irs
+        # ways=8: programs with few instances and many ops (here the 50k-200k-op
+        # ones) run as satellite kernels, 8 warps per group of 32 instances,
+        # beside the persistent kernel of the others
+        return Batch(irs, [N for _, N in sizes], dtype="f32", ways=8), time.perf_counter() - t0, irs
     ir3 = programs.quadrotor_mpc().to_bytes()
     ir1 = programs.quadrotor_lqr_step().to_bytes()
     srb = programs.srb_step().to_bytes()
@@ -357,11 +356,8 @@ def other_configs(dev, pk64, pk32, flush, reps, oracle_check=True):
           for j, (_, N) in enumerate(sizes)]
     outs = [torch.empty((32, N), dtype=torch.float32, device=dev) for _, N in sizes]
     by_block = {}
-    for blk in (32, 64, 128):            # cooperative programs allow 128-thread tiles only
-        try:
-            b.set_block(blk)
-        except Exception:
-            continue
+    for blk in (32, 64, 128):
+        b.set_block(blk)
         b(xs, outs, mode="persistent")
         by_block[blk] = _events_ms(lambda: b(xs, outs, mode="persistent"), reps, flush)
     block = min(by_block, key=by_block.get)
@@ -381,10 +377,11 @@ def other_configs(dev, pk64, pk32, flush, reps, oracle_check=True):
         "op_instances_generated": gen_ops, "persistent_ms": ms_p, "plain_8_launches_ms": ms_s,
         "speedup_persistent_vs_plain": ms_s / ms_p, "tile_block": block,
         "persistent_ms_by_tile_block": {str(k): v for k, v in by_block.items()},
-        "cooperative_tiles": "ways=4: the longest programs with N <= 8192 and >= 60,000 ops (at most "
-                             "three; here 100k, 150k, 200k) run 32 instances per 128-thread tile, "
-                             "4 warps splitting the program; their plain launch runs the same "
-                             "cooperative code", **b.info(),
+        "satellites": "ways=8: programs with N <= 8192 and >= 20,000 ops after the passes (here the "
+                      "50k-, 100k-, 150k- and 200k-op ones) run as cooperative kernels of their own, "
+                      "8 warps per group of 32 instances, on parallel graph branches beside the "
+                      "persistent kernel of the other four; their plain launch runs the same kernels",
+        **b.info(),
         "gop_per_s_generated": gen_ops / (ms_p * 1e-3) * 1e-9, "setup_seconds": t_compile}
     if oracle_check:
         b(xs, outs, mode="persistent")
@@ -496,22 +493,23 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2408_09662_gb300 import inputs, peaks, programs
-    from paper_2408_09662_gb300.api import tuned
+    from paper_2408_09662_gb300.tune import autotune
 
     ir = programs.random_program(N_OPS_GEN, seed=PROGRAM_SEED).to_bytes()
     x_np = inputs.normal(64, N_INST, seed=INPUT_SEED + rank)
     x64 = torch.tensor(x_np, dtype=torch.float64, device=dev)
     x32 = x64.float()
-    # launch configuration: one thread per instance (ways 0) or W warps sharing each
-    # group of 32 instances (cooperative kernels); "auto" lets api.tuned time the
-    # candidates once and keep the fastest, as Batch.tune does for the tile size
-    # FP64 with 2 warps per group measured 10.36 ms on one box and 11.0-11.1 ms on
-    # others (even within one run), so only the steady configurations compete
+    # launch configuration: the autotuner times one thread per instance (ways 0)
+    # against W warps sharing each group of 32 instances, then refines the
+    # faster shape (instances per thread, register caps, groups per CTA); every
+    # candidate runs this batch.  FP64 with 2 warps per group measured 10.36 ms
+    # on one box and 11.0-11.1 ms on others, so only the steady shapes compete.
     cand = {"f64": (0, 4) if args.ways64 == "auto" else (int(args.ways64),),
-            "f32": (0, 2, 4, 8) if args.ways32 == "auto" else (int(args.ways32),)}
-    fn64 = tuned(ir, x64, "f64", cand["f64"])      # one after the other: the timings
-    fn32 = tuned(ir, x32, "f32", cand["f32"])      # must not share the GPU
-    tuning = {dt: {"candidates_ms": {str(w): v for w, v in fn.tuning_ms.items()}, "ways": fn.ways}
+            "f32": (0, 4, 8) if args.ways32 == "auto" else (int(args.ways32),)}
+    fn64 = autotune(ir, x64, "f64", ways=cand["f64"], use_cache=False)   # one after the other:
+    fn32 = autotune(ir, x32, "f32", ways=cand["f32"], use_cache=False)   # nothing else on the GPU
+    tuning = {dt: {"chosen": fn.tune_record["options"],
+                   "candidates_ms": [[json.dumps(o, sort_keys=True), ms] for o, ms in fn.tune_record["candidates"]]}
               for dt, fn in (("f64", fn64), ("f32", fn32))}
 
     y64 = torch.empty((fn64.nnz_out, N_INST), dtype=torch.float64, device=dev)
@@ -598,6 +596,10 @@ def main():
 
     # ---- roofline: measured FMA rate and per-op weights -------------------------
     pk64, pk32 = peaks.cached_or_measure(torch.cuda.get_device_name(dev), reuse=args.no_peaks)
+    # the FP32 FMA chains once more, back to back for 1.5 s with the clocks sampled:
+    # the rate (and SM clock) a full FP32 FMA load sustains under the power cap
+    with ClockSampler(torch.cuda.current_device()) as clk_fma:
+        fma32_sustained = peaks.sustained_fma("f32", 1.5)
     w64 = peaks.weighted_ops(fn64.op_counts(), pk64["weights"])
     w32 = peaks.weighted_ops(fn32.op_counts(), pk32["weights"])
     t64, t32 = ms_per_step * 1e-3, ms32 * 1e-3
@@ -623,17 +625,22 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": dict(workload_config(fn64.info), ways_f64=tuning["f64"]["ways"],
-                       ways_f32=tuning["f32"]["ways"],
+        "config": dict(workload_config(fn64.info), launch_f64=tuning["f64"]["chosen"],
+                       launch_f32=tuning["f32"]["chosen"],
                        launch="ways = W: W warps share each group of 32 instances (cooperative "
-                              "kernel); ways = 0: one thread per instance"),
-        "ways_tuning_ms": tuning,
+                              "kernel), coop_groups such groups per CTA; ways = 0: one thread "
+                              "per instance, inst_per_thread instances each, maxrregcount a "
+                              "register cap"),
+        "launch_tuning_ms": tuning,
         "gop_per_s": ops_live * N_INST / t64 * 1e-9,
         "roofline": {"bound": "alu", "achieved": ach64 * 1e-12,
                      "peak": NOMINAL_FMA_PER_S["f64"] * 1e-12,
                      "unit": "TFMA/s (FMA-equivalent ops, FP64)",
                      "frac": ach64 / NOMINAL_FMA_PER_S["f64"],
                      "traffic": NCU_TRAFFIC.get(hashlib.sha256(fn64.source().encode()).hexdigest()[:16]),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this "
+                                       "kernel's source hash; null: no capture of the current source",
+                     "kernel_source_hash": hashlib.sha256(fn64.source().encode()).hexdigest()[:16],
                      "algorithmic_bytes": int((fn64.nnz_in + fn64.nnz_out) * 8 * N_INST),
                      "peak_source": "derived: FP64 1.25 TFLOP/s = 0.625 TFMA/s (2 FMA/clk/SM x 152 SMs "
                                     "x 2.07 GHz)",
@@ -650,6 +657,8 @@ def main():
                               "peak_source": "derived: 128 FMA/clk/SM x 152 SMs x 2.07 GHz",
                               "peak_measured": pk32["fma_per_s"] * 1e-12,
                               "frac_of_measured": ach32 / pk32["fma_per_s"],
+                              "peak_sustained_fma_chains": fma32_sustained * 1e-12,
+                              "clocks_under_fma_chains": clk_fma.summary(),
                               "work_per_instance_fma_eq": w32},
                  "err_vs_fp64_kernel": {"max_rel_scaled": float(rel32.max()),
                                         "median_rel_scaled": float(np.median(rel32)),

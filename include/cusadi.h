@@ -75,11 +75,15 @@ typedef struct {
   int64_t segment_ops;        /* compiled programs are split into kernels of at most this
                                  many ops, compiled in parallel                  (40000) */
   int32_t block;              /* threads per block of compiled kernels, multiple of 32 (128) */
-  int32_t maxrregcount;       /* register cap for compiled kernels, 0 = compiler's choice */
+  int32_t maxrregcount;       /* register cap for compiled kernels (enforced through their
+                                 launch bounds: at least 65536 / (CTA threads * cap)
+                                 resident CTAs per SM), 0 = compiler's choice */
   int32_t fmad;               /* 1: let the compiler contract a*b+c into fma     (1) */
   int32_t compile_threads;    /* parallel NVRTC compiles, 0 = all host cores */
   int32_t schedule;           /* 1: reorder ops to lower register pressure       (1) */
-  int32_t inline_math;        /* 1: inline transcendental functions (slow compile) (0) */
+  int32_t inline_math;        /* 1: inline every math function (slow compile); 2: inline the
+                                 short ones (exp, expm1, log, log1p) and call the rest;
+                                 0: every transcendental is an out-of-line call    (0) */
   int32_t adjoint;            /* 1: build the adjoint kernels at load; 0: at the first call
                                  that needs them (cusadi_adjoint and friends)   (0) */
   int32_t ways;               /* 2..16: within-instance parallelism on the compiled path
@@ -107,6 +111,10 @@ typedef struct {
                                  after every this many ops, so the CTA's warps stay in
                                  the same stretch of a long kernel's code (instruction
                                  cache reuse); 0: no barriers                       (0) */
+  int32_t interp_shared_kb;   /* interpreter path: shared memory per 128-thread CTA for the
+                                 work slots, in KB (0..200); the slots of the values that
+                                 do not fit, chosen by linear scan as the ones read
+                                 last, live in the workspace                       (96) */
   const char* cache_dir;      /* directory for compiled kernels, NULL = in-memory only */
 } cusadi_options;
 
@@ -352,25 +360,25 @@ cusadi_status cusadi_densify(cusadi_fn fn, int arg, const void* y, int64_t ld_y,
  * once and the short ones fill the GPU around them.  The launch (ticket reset +
  * kernel) is captured once per device in a CUDA graph and replayed.  The same
  * link also has one plain kernel per program (CUSADI_BATCH_PLAIN), so the two
- * modes run identical per-instance code and give bit-identical results. */
-#define CUSADI_BATCH_PERSISTENT 0  /* one graph launch of the scheduler kernel */
-#define CUSADI_BATCH_PLAIN 1       /* one kernel launch per program, in order */
+ * modes run identical per-instance code and give bit-identical results.
+ *
+ * With ways = W > 1, programs with at most 8,192 instances and at least 20,000
+ * ops (after the passes) become satellites: each is compiled on its own as a
+ * cooperative kernel, W warps splitting the program over each group of 32
+ * instances (parallelism inside one expression graph, which CusADi leaves to
+ * future work, §VI), and the batch's graph runs them on parallel branches
+ * beside the scheduler kernel, started first.  Such a long program with few
+ * instances then stops setting the length of the launch.  Its plain mode
+ * launches the same cooperative kernels. */
+#define CUSADI_BATCH_PERSISTENT 0  /* one graph launch: satellites + scheduler kernel */
+#define CUSADI_BATCH_PLAIN 1       /* one kernel launch per program (segment), in order */
 
 /* Compiles and links n programs (irs[j] of nbytes[j] bytes) for N[j]
  * instances each.  opt: dtype, block (32, 64 or 128: instances per tile),
- * maxrregcount, fmad, schedule, segment_ops, compile_threads, cache_dir;
- * path and compile_limit_ops are ignored (always compiled).  ways: 0, or 4 to
- * give the longest programs with N[j] <= 8192 and >= 60,000 ops (at most
- * three, 450,000 ops in all: larger sets made nvJitLink fail) cooperative
- * tiles: the
- * 128-thread scheduler then runs such a program 32 instances per tile with
- * its 4 warps splitting the program between them (parallelism inside one
- * expression graph, which CusADi leaves to future work, §VI), so a long
- * program with few instances stops setting the length of the launch.  Such
- * a program is compiled in cooperative form only: its plain launch (mode
- * CUSADI_BATCH_PLAIN) runs the same code, 32 instances per 128-thread CTA,
- * and the batch then runs 128-thread tiles only (cusadi_batch_set_block
- * refuses 32 and 64).  n <= 32.  Errors: INVALID_ARG, INVALID_IR, COMPILE, OOM. */
+ * maxrregcount, fmad, schedule, segment_ops, compile_threads, cache_dir, and
+ * ways (0, or 2..16 warps per group of the satellite kernels); path and
+ * compile_limit_ops are ignored (always compiled).  n <= 32.  Errors:
+ * INVALID_ARG, INVALID_IR, COMPILE, OOM. */
 cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, const int64_t* N,
                                   int n, const cusadi_options* opt, cusadi_batch* out);
 void cusadi_batch_free(cusadi_batch b);
@@ -381,9 +389,11 @@ size_t cusadi_batch_workspace_bytes(cusadi_batch b);
 /* Evaluates every program: in[j] / out[j] are [nnz_in_j x ld_in[j]] and
  * [nnz_out_j x ld_out[j]] device buffers (ld >= N[j]) as for cusadi_eval.
  * mode: CUSADI_BATCH_PERSISTENT or CUSADI_BATCH_PLAIN.  The first call on a
- * device loads the module, uploads the tile table and captures the graph
- * (allocates; not capturable); later calls only copy the buffer table when
- * it changed (a few hundred bytes) and launch.  The buffer table and the tile
+ * device loads the modules and uploads the tile table (allocates; not
+ * capturable); the first persistent call captures the graph.  Later calls
+ * only copy the buffer table when it changed (a few hundred bytes; with
+ * satellites the graph is then captured again, since their launches carry
+ * the buffers' addresses) and launch.  The buffer table and the tile
  * counter belong to the batch (one per device), so calls on one batch must not
  * overlap on the GPU: issue them on one stream, or order them with events. */
 cusadi_status cusadi_batch_eval(cusadi_batch b, const void* const* in, const int64_t* ld_in,
@@ -391,8 +401,7 @@ cusadi_status cusadi_batch_eval(cusadi_batch b, const void* const* in, const int
                                 int mode, cusadi_stream stream);
 
 /* Selects the tile size (32, 64 or 128 instances = threads per CTA) of the
- * persistent launch; the link holds all three.  INVALID_ARG for other sizes,
- * and for 32 or 64 when the batch has cooperative programs (ways = 4). */
+ * persistent launch; the link holds all three.  INVALID_ARG for other sizes. */
 cusadi_status cusadi_batch_set_block(cusadi_batch b, int block);
 
 /* Tile count, threads per CTA, persistent grid size (0 before the first

@@ -283,7 +283,10 @@ def tuned(program, x: torch.Tensor, dtype: str = "f64", candidates=(0, 2, 4), re
 class Batch:
     """Several programs, each over its own fixed instance count, evaluated by one
     persistent kernel replayed from a CUDA graph (mode "persistent") or by one
-    plain kernel per program (mode "plain"); both run the same per-instance code."""
+    plain kernel per program (mode "plain"); both run the same per-instance code.
+    With ways = W > 1, long programs with few instances run as cooperative
+    satellite kernels (W warps per group of 32 instances) beside the
+    persistent kernel, on parallel branches of the same graph."""
 
     MODES = {"persistent": L.CUSADI_BATCH_PERSISTENT, "plain": L.CUSADI_BATCH_PLAIN}
 
@@ -353,10 +356,7 @@ class Batch:
         """Times the persistent launch at each tile size and keeps the fastest."""
         best = None
         for block in (32, 64, 128):
-            try:
-                self.set_block(block)
-            except L.CusadiError:      # cooperative programs: 128-thread tiles only
-                continue
+            self.set_block(block)
             self(xs, outs)
             torch.cuda.synchronize()
             ts = []

@@ -6,6 +6,9 @@
 // one-instance device functions, linked with a scheduler kernel whose CTAs
 // take tiles (program, consecutive instances) from an atomic ticket in
 // longest-program-first order, and the launch is replayed from a CUDA graph.
+// Long programs with few instances ("satellites", with ways > 1) run instead
+// as cooperative kernels of their own, W warps per group of 32 instances, on
+// parallel branches of the same graph, started before the scheduler kernel.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <nvJitLink.h>
@@ -13,6 +16,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -49,29 +53,26 @@ struct BArg {
 struct BatchProg {
   IRFile ir;
   Graph g;
-  CodegenResult cg;
+  CodegenResult cg;              // one-instance device functions (linked, scheduler tiles)
   std::vector<std::string> bins;
-  CodegenResult ccg;             // cooperative device functions (4 warps per 32 instances)
-  std::vector<std::string> cbins;
-  bool coop = false;
+  CodegenResult scg;             // satellite: standalone cooperative kernels
+  std::vector<std::string> sbins;
+  bool sat = false;
   int64_t N = 0, n_ops = 0;
   size_t ws_off = 0;
   int64_t ldw = 0;
 };
 
-// Cooperative tiles: in the 128-thread scheduler, a program with few
-// instances and many ops is run 32 instances per tile by the CTA's 4 warps
-// together (within-instance parallelism), so its tiles stop being the longest
-// chains of the launch.
-constexpr int kCoopWays = 4;
-constexpr int kCoopVariant = 2;                  // the 128-thread scheduler
-// Which programs: at most N = 8192 instances and at least 60,000 ops, the
-// longest first, at most three and 450,000 ops in all.  The caps are measured:
-// nvJitLink (CUDA 13.0) failed inside nvJitLinkComplete when four programs of
-// 50k-200k ops were linked in cooperative form, while any three linked.
-constexpr int64_t kCoopMaxN = 8192, kCoopMinOps = 60000, kCoopMaxTotalOps = 450000;
-constexpr int kCoopMaxProgs = 3;
-constexpr int kCoopSharedKB = 96;
+// Satellites: a program with few instances and many ops would set the length
+// of the persistent launch (its tiles are the longest chains), so with
+// ways = W > 1 it runs as its own cooperative kernel, W warps splitting the
+// program over each group of 32 instances (within-instance parallelism), in a
+// module of its own (not linked with the scheduler, so it does not raise the
+// scheduler's register count), concurrently with the scheduler kernel.
+// Which programs: at most 8,192 instances and at least 20,000 ops (after the
+// passes): then the one-thread tiles of the program hold fewer warps than the
+// GPU has SMs while each runs for as long as a whole many-instance program.
+constexpr int64_t kSatMaxN = 8192, kSatMinOps = 20000;
 
 struct BatchDev {
   bool ready = false;
@@ -80,12 +81,18 @@ struct BatchDev {
   std::vector<CUfunction> plain;
   int grid[kVariants] = {};
   void* d_tiles[kVariants] = {};
-  unsigned smem = 0;                         // dynamic shared memory of the 128-thread scheduler
   unsigned* d_ticket = nullptr;
   BArg* d_args = nullptr;
   std::vector<BArg> last;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec[kVariants] = {};
+  bool captured = false;                     // exec[] hold the current buffers' launches
+  // satellites (per program; empty for scheduler programs)
+  std::vector<CUmodule> sat_mods;
+  std::vector<std::vector<CUfunction>> sat_fn;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
 };
 
 cusadi_status bfail(cusadi_status s, const std::string& m) { return report(s, m); }
@@ -100,8 +107,7 @@ struct cusadi_batch_s {
   std::vector<BTile> tiles[kVariants];
   int variant = 2;
   size_t ws_bytes = 0;
-  int64_t coop_smem = 0;         // largest shared-memory need of a cooperative program
-  bool has_coop = false;         // then only the 128-thread scheduler has tiles
+  int n_sat = 0;                 // programs run as satellites
   int registers = 0;
   std::mutex mu;
   std::map<int, BatchDev> dev;
@@ -125,28 +131,10 @@ std::string scheduler_source(const cusadi_batch_s& b) {
       s << "extern \"C\" __device__ void " << seg.name << "(const " << T << "* __restrict__, long long, const "
         << T << "* __restrict__, long long, " << T << "* __restrict__, long long, " << TW
         << "* __restrict__, long long, long long);\n";
-  for (size_t p = 0; p < b.progs.size(); ++p)
-    for (auto& seg : b.progs[p].ccg.segs)
-      s << "extern \"C\" __device__ void " << seg.name << "(const " << T << "* __restrict__, long long, "
-        << T << "* __restrict__, long long, " << TW << "* __restrict__, long long, long long, int, "
-        << "unsigned char* __restrict__);\n";
-  s << "static __device__ __forceinline__ void cs_run_coop(const BArg* __restrict__ A, int p, "
-    << "long long first, int count, unsigned char* smem) {\n  switch (p) {\n";
-  for (size_t p = 0; p < b.progs.size(); ++p) {
-    if (!b.progs[p].coop) continue;
-    s << "    case " << p << ": {\n      const BArg a = A[" << p << "];\n";
-    for (auto& seg : b.progs[p].ccg.segs)
-      s << "      " << seg.name << "(a.X, a.ldx, a.Y, a.ldy, a.W, a.ldw, first, count, smem);\n";
-    s << "      break;\n    }\n";
-  }
-  s << "  }\n}\n";
-  s << "__device__ __constant__ unsigned char cs_coop[" << std::max<size_t>(b.progs.size(), 1) << "] = {";
-  for (size_t p = 0; p < b.progs.size(); ++p) s << (p ? ", " : "") << (b.progs[p].coop ? 1 : 0);
-  s << "};\n";
   s << "static __device__ __forceinline__ void cs_run(const BArg* __restrict__ A, int p, long long i) {\n"
     << "  switch (p) {\n";
   for (size_t p = 0; p < b.progs.size(); ++p) {
-    if (b.progs[p].coop) continue;
+    if (b.progs[p].sat) continue;
     s << "    case " << p << ": {\n      const BArg a = A[" << p << "];\n";
     for (auto& seg : b.progs[p].cg.segs)
       s << "      " << seg.name << "(a.X, a.ldx, a.X, a.ldx, a.Y, a.ldy, a.W, a.ldw, i);\n";
@@ -155,36 +143,26 @@ std::string scheduler_source(const cusadi_batch_s& b) {
   s << "  }\n}\n";
   for (int v = 0; v < kVariants; ++v) {
     const int B = kBlocks[v];
-    const bool coop = v == kCoopVariant;
     s << "extern \"C\" __global__ void __launch_bounds__(" << B << ") cs_batch_" << B
       << "(const BTile* __restrict__ tiles, int n_tiles, unsigned int* ticket,\n"
       << "    const BArg* __restrict__ A) {\n"
-      << "  __shared__ int s_t;\n";
-    if (coop) s << "  extern __shared__ __align__(16) unsigned char cs_dyn[];\n";
-    s << "  for (;;) {\n"
+      << "  __shared__ int s_t;\n"
+      << "  for (;;) {\n"
       << "    if (threadIdx.x == 0) s_t = (int)atomicAdd(ticket, 1u);\n"
       << "    __syncthreads();\n"
       << "    const int t = s_t;\n"
       << "    __syncthreads();\n"
       << "    if (t >= n_tiles) return;\n"
-      << "    const BTile tl = tiles[t];\n";
-    if (coop)   // the tile is the same for the whole CTA, so every thread takes the same branch
-      s << "    if (cs_coop[tl.prog]) cs_run_coop(A, tl.prog, tl.first, tl.count, cs_dyn);\n"
-        << "    else if ((int)threadIdx.x < tl.count) cs_run(A, tl.prog, tl.first + threadIdx.x);\n";
-    else
-      s << "    if ((int)threadIdx.x < tl.count) cs_run(A, tl.prog, tl.first + threadIdx.x);\n";
-    s << "  }\n}\n";
+      << "    const BTile tl = tiles[t];\n"
+      << "    if ((int)threadIdx.x < tl.count) cs_run(A, tl.prog, tl.first + threadIdx.x);\n"
+      << "  }\n}\n";
   }
   for (size_t p = 0; p < b.progs.size(); ++p) {
+    if (b.progs[p].sat) continue;
     s << "extern \"C\" __global__ void __launch_bounds__(128) cs_plain_" << p
-      << "(const BArg* __restrict__ A, long long N) {\n";
-    if (b.progs[p].coop)   // one group of 32 instances per CTA of 4 warps
-      s << "  extern __shared__ __align__(16) unsigned char cs_dyn[];\n"
-        << "  const long long first = (long long)blockIdx.x * 32;\n"
-        << "  cs_run_coop(A, " << p << ", first, (int)(N - first < 32 ? N - first : 32), cs_dyn);\n}\n";
-    else
-      s << "  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n"
-        << "  if (i < N) cs_run(A, " << p << ", i);\n}\n";
+      << "(const BArg* __restrict__ A, long long N) {\n"
+      << "  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n"
+      << "  if (i < N) cs_run(A, " << p << ", i);\n}\n";
   }
   return s.str();
 }
@@ -234,57 +212,136 @@ cusadi_status batch_device(cusadi_batch b, BatchDev** out) {
   if (r != CUDA_SUCCESS) return bfail(CUSADI_E_CUDA, "cuModuleLoadData failed: " + std::to_string(r));
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  d.smem = (unsigned)b->coop_smem;
   for (int v = 0; v < kVariants; ++v) {
     std::string nm = "cs_batch_" + std::to_string(kBlocks[v]);
     if ((r = D.moduleGetFunction(&d.persist[v], d.mod, nm.c_str())) != CUDA_SUCCESS)
       return bfail(CUSADI_E_CUDA, "missing " + nm);
-    const unsigned smem = v == kCoopVariant ? d.smem : 0;
-    if (smem > 48 * 1024 &&
-        (r = D.funcSetAttribute(d.persist[v], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem)) != CUDA_SUCCESS)
-      return bfail(CUSADI_E_CUDA, "cuFuncSetAttribute failed: " + std::to_string(r));
     int per_sm = 0;
-    D.occupancy(&per_sm, d.persist[v], kBlocks[v], smem);
+    D.occupancy(&per_sm, d.persist[v], kBlocks[v], 0);
     const int64_t nt = (int64_t)b->tiles[v].size();
-    d.grid[v] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), nt));
+    // with satellites, the scheduler kernel takes the SMs in proportion to its
+    // share of the work (ops x instances), so the satellites find SMs free
+    // whichever of them the GPU starts first
+    int64_t sm_share = sms;
+    if (b->n_sat > 0) {
+      double reg = 0, sat = 0;
+      for (const BatchProg& P : b->progs) (P.sat ? sat : reg) += (double)P.n_ops * (double)P.N;
+      sm_share = std::max<int64_t>(1, (int64_t)std::llround(sms * reg / std::max(reg + sat, 1.0)));
+    }
+    d.grid[v] = (int)std::max<int64_t>(1, std::min<int64_t>(sm_share * std::max(per_sm, 1), nt));
     size_t tb = std::max<size_t>(1, b->tiles[v].size()) * sizeof(BTile);
     if ((ce = cudaMalloc(&d.d_tiles[v], tb)) != cudaSuccess) return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
     if (!b->tiles[v].empty())
       cudaMemcpy(d.d_tiles[v], b->tiles[v].data(), b->tiles[v].size() * sizeof(BTile), cudaMemcpyHostToDevice);
   }
-  d.plain.resize(b->progs.size());
+  d.plain.assign(b->progs.size(), nullptr);
+  d.sat_fn.assign(b->progs.size(), {});
   for (size_t p = 0; p < b->progs.size(); ++p) {
-    std::string nm = "cs_plain_" + std::to_string(p);
-    if ((r = D.moduleGetFunction(&d.plain[p], d.mod, nm.c_str())) != CUDA_SUCCESS)
-      return bfail(CUSADI_E_CUDA, "missing " + nm);
-    if (b->progs[p].coop && d.smem > 48 * 1024 &&
-        (r = D.funcSetAttribute(d.plain[p], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)d.smem)) != CUDA_SUCCESS)
-      return bfail(CUSADI_E_CUDA, "cuFuncSetAttribute failed: " + std::to_string(r));
+    const BatchProg& P = b->progs[p];
+    if (!P.sat) {
+      std::string nm = "cs_plain_" + std::to_string(p);
+      if ((r = D.moduleGetFunction(&d.plain[p], d.mod, nm.c_str())) != CUDA_SUCCESS)
+        return bfail(CUSADI_E_CUDA, "missing " + nm);
+      continue;
+    }
+    for (size_t k = 0; k < P.sbins.size(); ++k) {
+      CUmodule m;
+      if ((r = D.moduleLoadData(&m, P.sbins[k].data())) != CUDA_SUCCESS)
+        return bfail(CUSADI_E_CUDA, "cuModuleLoadData (satellite) failed: " + std::to_string(r));
+      d.sat_mods.push_back(m);
+      CUfunction f;
+      if ((r = D.moduleGetFunction(&f, m, P.scg.segs[k].name.c_str())) != CUDA_SUCCESS)
+        return bfail(CUSADI_E_CUDA, "missing " + P.scg.segs[k].name);
+      if (P.scg.smem_bytes > 48 * 1024 &&
+          (r = D.funcSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)P.scg.smem_bytes)) != CUDA_SUCCESS)
+        return bfail(CUSADI_E_CUDA, "cuFuncSetAttribute failed: " + std::to_string(r));
+      d.sat_fn[p].push_back(f);
+    }
   }
   if ((ce = cudaMalloc((void**)&d.d_ticket, 256)) != cudaSuccess) return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
   if ((ce = cudaMalloc((void**)&d.d_args, kMaxProgs * sizeof(BArg))) != cudaSuccess)
     return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
   if ((ce = cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking)) != cudaSuccess)
     return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
-  // one graph per tile size: reset the ticket, run the scheduler kernel
+  if (b->n_sat > 0) {
+    if ((ce = cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming)) != cudaSuccess)
+      return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
+    for (int k = 0; k < b->n_sat; ++k) {
+      cudaStream_t st;
+      cudaEvent_t ev;
+      if ((ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
+        return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
+      d.side.push_back(st);
+      if ((ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
+      d.join.push_back(ev);
+    }
+  }
+  d.ready = true;
+  *out = &d;
+  return CUSADI_OK;
+}
+
+// Launches satellite p's kernels (one per segment, in order) on `st`.
+cusadi_status launch_satellite(cusadi_batch b, BatchDev& d, size_t p, const BArg& a, cudaStream_t st) {
+  const BatchProg& P = b->progs[p];
+  const void* X = a.X;
+  void* Y = a.Y;
+  void* W = a.W;
+  long long ldx = a.ldx, ldy = a.ldy, n = P.N, ldw = a.ldw;
+  int acc = 0, reduce = 0, vec = 0;
+  for (CUfunction f : d.sat_fn[p]) {
+    void* args[] = {(void*)&X, &ldx, (void*)&X, &ldx, &Y, &ldy, &n, &W, &ldw, &acc, &reduce, &vec};
+    CUresult r = driver().launchKernel(f, (unsigned)((P.N + 31) / 32), 1, 1, 32u * (unsigned)P.scg.coop_ways, 1, 1,
+                                       (unsigned)P.scg.smem_bytes, (CUstream)st, args, nullptr);
+    if (r != CUDA_SUCCESS) return bfail(CUSADI_E_CUDA, "cuLaunchKernel (satellite) failed: " + std::to_string(r));
+  }
+  return CUSADI_OK;
+}
+
+// One graph per tile size: reset the ticket; fork the satellites onto side
+// streams (their kernels carry the buffers' addresses, so a change of buffers
+// re-captures); run the scheduler kernel; join.
+cusadi_status capture_graphs(cusadi_batch b, BatchDev& d, const std::vector<BArg>& args) {
+  for (int v = 0; v < kVariants; ++v)
+    if (d.exec[v]) { cudaGraphExecDestroy(d.exec[v]); d.exec[v] = nullptr; }
+  d.captured = false;
+  const Driver& D = driver();
   for (int v = 0; v < kVariants; ++v) {
     cudaGraph_t g;
-    if ((ce = cudaStreamBeginCapture(d.cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-      return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
-    cudaMemsetAsync(d.d_ticket, 0, sizeof(unsigned), d.cap);
+    cudaError_t ce = cudaStreamBeginCapture(d.cap, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return bfail(CUSADI_E_CUDA, cudaGetErrorString(ce));
+    bool ok = cudaMemsetAsync(d.d_ticket, 0, sizeof(unsigned), d.cap) == cudaSuccess;
+    if (b->n_sat > 0) ok = ok && cudaEventRecord(d.fork, d.cap) == cudaSuccess;
+    std::vector<size_t> sats;                        // longest first
+    for (size_t p = 0; p < b->progs.size(); ++p)
+      if (b->progs[p].sat) sats.push_back(p);
+    std::stable_sort(sats.begin(), sats.end(),
+                     [&](size_t a, size_t c) { return b->progs[a].n_ops > b->progs[c].n_ops; });
+    int k = 0;
+    for (size_t p : sats) {
+      if (!ok) break;
+      ok = cudaStreamWaitEvent(d.side[k], d.fork, 0) == cudaSuccess &&
+           launch_satellite(b, d, p, args[p], d.side[k]) == CUSADI_OK &&
+           cudaEventRecord(d.join[k], d.side[k]) == cudaSuccess;
+      ++k;
+    }
     int nt = (int)b->tiles[v].size();
-    void* args[] = {&d.d_tiles[v], &nt, &d.d_ticket, &d.d_args};
-    r = D.launchKernel(d.persist[v], (unsigned)d.grid[v], 1, 1, (unsigned)kBlocks[v], 1, 1,
-                       v == kCoopVariant ? d.smem : 0u, (CUstream)d.cap, args, nullptr);
+    CUresult r = CUDA_SUCCESS;
+    if (ok && nt > 0) {
+      void* kargs[] = {&d.d_tiles[v], &nt, &d.d_ticket, &d.d_args};
+      r = D.launchKernel(d.persist[v], (unsigned)d.grid[v], 1, 1, (unsigned)kBlocks[v], 1, 1, 0u,
+                         (CUstream)d.cap, kargs, nullptr);
+    }
+    for (int j = 0; ok && j < k; ++j) ok = cudaStreamWaitEvent(d.cap, d.join[j], 0) == cudaSuccess;
     ce = cudaStreamEndCapture(d.cap, &g);
-    if (r != CUDA_SUCCESS || ce != cudaSuccess)
+    if (!ok || r != CUDA_SUCCESS || ce != cudaSuccess)
       return bfail(CUSADI_E_CUDA, "capturing the batch launch failed");
     ce = cudaGraphInstantiate(&d.exec[v], g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return bfail(CUSADI_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
   }
-  d.ready = true;
-  *out = &d;
+  d.captured = true;
   return CUSADI_OK;
 }
 
@@ -310,8 +367,8 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
   for (int v = 0; v < kVariants; ++v)
     if (o.block == kBlocks[v]) b->variant = v;
   if (b->variant < 0) return bfail(CUSADI_E_INVALID_ARG, "batch block must be 32, 64 or 128");
-  if (o.ways != 0 && o.ways != kCoopWays)
-    return bfail(CUSADI_E_INVALID_ARG, "batch ways must be 0 or 4 (4 warps of the 128-thread scheduler)");
+  if (o.ways < 0 || o.ways == 1 || o.ways > 16)
+    return bfail(CUSADI_E_INVALID_ARG, "batch ways must be 0 or 2..16");
   b->progs.resize(n);
   const size_t elt_ws = o.dtype == CUSADI_F32 ? 4 : 8;
   try {
@@ -328,51 +385,43 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
       P.n_ops = count_ops(P.g);
       P.N = N[p];
     }
-    if (o.ways == kCoopWays) {
-      std::vector<int> cand;
-      for (int p = 0; p < n; ++p)
-        if (b->progs[p].N <= kCoopMaxN && b->progs[p].n_ops >= kCoopMinOps) cand.push_back(p);
-      std::stable_sort(cand.begin(), cand.end(),
-                       [&](int a, int c) { return b->progs[a].n_ops > b->progs[c].n_ops; });
-      int64_t total = 0;
-      int taken = 0;
-      for (int p : cand)
-        if (taken < kCoopMaxProgs && total + b->progs[p].n_ops <= kCoopMaxTotalOps) {
-          b->progs[p].coop = true;
-          total += b->progs[p].n_ops;
-          ++taken;
-        }
-    }
+    for (int p = 0; p < n; ++p)
+      if (o.ways > 1 && b->progs[p].N <= kSatMaxN && b->progs[p].n_ops >= kSatMinOps) {
+        b->progs[p].sat = true;
+        ++b->n_sat;
+      }
     for (int p = 0; p < n; ++p) {
       BatchProg& P = b->progs[p];
       CodegenOptions co;
       co.dtype = o.dtype;
       co.segment_ops = o.segment_ops;
-      co.inline_math = o.inline_math != 0;
+      co.inline_math = o.inline_math;
       co.own_math = o.own_math;
       co.device_fn = true;
       co.prefix = "cs_b" + std::to_string(p);
-      // a cooperative program is linked in cooperative form only
-      if (!P.coop) P.cg = generate(P.g, co);
-      if (P.coop) {
-        b->has_coop = true;
-        b->variant = kCoopVariant;
+      if (!P.sat) {
+        P.cg = generate(P.g, co);
+      } else {
+        // standalone kernels: W warps per group of 32 instances, one group per CTA
         CodegenOptions cc = co;
-        cc.prefix = "cs_bc" + std::to_string(p);
-        cc.coop_shared_kb = kCoopSharedKB;
-        P.ccg = generate_coop(P.g, cc, plan_coop(P.g, kCoopWays, 8.0));
-        b->coop_smem = std::max(b->coop_smem, P.ccg.smem_bytes);
+        cc.device_fn = false;
+        cc.prefix = "cs_bs" + std::to_string(p);
+        cc.maxrregcount = o.maxrregcount;
+        P.scg = generate_coop(P.g, cc, plan_coop(P.g, o.ways, 8.0));
       }
       P.ldw = (P.N + 31) / 32 * 32;
       b->ws_bytes = (b->ws_bytes + 255) / 256 * 256;
       P.ws_off = b->ws_bytes;
-      b->ws_bytes += (size_t)std::max(P.cg.ws_rows, P.ccg.ws_rows) * P.ldw * elt_ws;
+      b->ws_bytes += (size_t)std::max(P.cg.ws_rows, P.scg.ws_rows) * P.ldw * elt_ws;
     }
   } catch (const std::bad_alloc&) {
     return bfail(CUSADI_E_OOM, "out of host memory");
   }
   // compile every segment (all programs) in parallel, then the scheduler, then link
-  struct Job { const std::string* src; const std::string* name; std::string* bin; std::string log; bool ok; };
+  struct Job {
+    const std::string* src; const std::string* name; std::string* bin; std::string log; bool ok;
+    bool standalone = false;    // a satellite kernel: its own module, not relocatable
+  };
   std::vector<std::string> sched(1);
   std::string sched_src = scheduler_source(*b), sched_name = "cs_batch_sched";
   std::vector<Job> jobs;
@@ -380,15 +429,18 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
     P.bins.assign(P.cg.segs.size(), std::string());
     for (size_t s = 0; s < P.cg.segs.size(); ++s)
       jobs.push_back({&P.cg.segs[s].source, &P.cg.segs[s].name, &P.bins[s], "", false});
-    P.cbins.assign(P.ccg.segs.size(), std::string());
-    for (size_t s = 0; s < P.ccg.segs.size(); ++s)
-      jobs.push_back({&P.ccg.segs[s].source, &P.ccg.segs[s].name, &P.cbins[s], "", false});
+    P.sbins.assign(P.scg.segs.size(), std::string());
+    for (size_t s = 0; s < P.scg.segs.size(); ++s)
+      jobs.push_back({&P.scg.segs[s].source, &P.scg.segs[s].name, &P.sbins[s], "", false, true});
   }
   jobs.push_back({&sched_src, &sched_name, &sched[0], "", false});
   std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo",
                                    "-DNDEBUG", "--relocatable-device-code=true"};
   opts.push_back(o.fmad ? "--fmad=true" : "--fmad=false");
   if (o.maxrregcount > 0) opts.push_back("--maxrregcount=" + std::to_string(o.maxrregcount));
+  std::vector<std::string> sopts;
+  for (auto& x : opts)
+    if (x != "--relocatable-device-code=true") sopts.push_back(x);
   // biggest first, so the longest compile starts at once
   std::vector<size_t> order(jobs.size());
   std::iota(order.begin(), order.end(), 0);
@@ -400,7 +452,7 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
   auto work = [&] {
     for (size_t k; (k = next.fetch_add(1)) < order.size();) {
       Job& j = jobs[order[k]];
-      j.ok = compile_nvrtc(*j.src, *j.name, opts, cache, *j.bin, j.log);
+      j.ok = compile_nvrtc(*j.src, *j.name, j.standalone ? sopts : opts, cache, *j.bin, j.log);
     }
   };
   std::vector<std::thread> th;
@@ -411,7 +463,6 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
   std::vector<std::string> objs;
   for (auto& P : b->progs) {
     for (auto& x : P.bins) objs.push_back(x);
-    for (auto& x : P.cbins) objs.push_back(x);
   }
   objs.push_back(sched[0]);
   std::string log;
@@ -420,14 +471,13 @@ cusadi_status cusadi_batch_create(const void* const* irs, const size_t* nbytes, 
   std::vector<int> byops(n);
   std::iota(byops.begin(), byops.end(), 0);
   std::stable_sort(byops.begin(), byops.end(), [&](int a, int c) { return b->progs[a].n_ops > b->progs[c].n_ops; });
-  for (int v = 0; v < kVariants; ++v) {
-    if (b->has_coop && v != kCoopVariant) continue;
+  for (int v = 0; v < kVariants; ++v)
     for (int p : byops) {
-      const int64_t t = v == kCoopVariant && b->progs[p].coop ? 32 : kBlocks[v];
+      if (b->progs[p].sat) continue;
+      const int64_t t = kBlocks[v];
       for (int64_t f = 0; f < b->progs[p].N; f += t)
         b->tiles[v].push_back({p, (int32_t)std::min<int64_t>(t, b->progs[p].N - f), f});
     }
-  }
   *out = b.release();
   return CUSADI_OK;
 }
@@ -444,7 +494,12 @@ void cusadi_batch_free(cusadi_batch b) {
     if (d.d_ticket) cudaFree(d.d_ticket);
     if (d.d_args) cudaFree(d.d_args);
     if (d.cap) cudaStreamDestroy(d.cap);
+    for (cudaStream_t st : d.side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : d.join) cudaEventDestroy(ev);
+    if (d.fork) cudaEventDestroy(d.fork);
     if (d.mod && driver().ok) driver().moduleUnload(d.mod);
+    for (CUmodule m : d.sat_mods)
+      if (driver().ok) driver().moduleUnload(m);
   }
   delete b;
 }
@@ -455,8 +510,6 @@ cusadi_status cusadi_batch_set_block(cusadi_batch b, int block) {
   if (!b) return bfail(CUSADI_E_INVALID_ARG, "NULL batch");
   for (int v = 0; v < kVariants; ++v)
     if (block == kBlocks[v]) {
-      if (b->has_coop && v != kCoopVariant)
-        return bfail(CUSADI_E_INVALID_ARG, "a batch with cooperative programs runs 128-thread tiles only");
       b->variant = v;
       return CUSADI_OK;
     }
@@ -491,18 +544,28 @@ cusadi_status cusadi_batch_eval(cusadi_batch b, const void* const* in, const int
     cudaError_t ce = cudaMemcpyAsync(d->d_args, args.data(), n * sizeof(BArg), cudaMemcpyHostToDevice, st);
     if (ce != cudaSuccess) return bfail(CUSADI_E_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(ce));
     d->last = args;
+    if (b->n_sat > 0) d->captured = false;   // the satellites' launches carry the addresses
   }
   if (mode == CUSADI_BATCH_PERSISTENT) {
+    if (!d->captured) {
+      std::lock_guard<std::mutex> lk(b->mu);
+      s = capture_graphs(b, *d, args);
+      if (s != CUSADI_OK) return s;
+    }
     cudaError_t ce = cudaGraphLaunch(d->exec[b->variant], st);
     if (ce != cudaSuccess) return bfail(CUSADI_E_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(ce));
     return CUSADI_OK;
   }
   for (size_t p = 0; p < n; ++p) {
+    if (b->progs[p].sat) {
+      s = launch_satellite(b, *d, p, args[p], st);
+      if (s != CUSADI_OK) return s;
+      continue;
+    }
     long long N = b->progs[p].N;
     void* a[] = {&d->d_args, &N};
-    const bool coop = b->progs[p].coop;
-    CUresult r = driver().launchKernel(d->plain[p], (unsigned)(coop ? (N + 31) / 32 : (N + 127) / 128),
-                                       1, 1, 128, 1, 1, coop ? d->smem : 0u, (CUstream)st, a, nullptr);
+    CUresult r = driver().launchKernel(d->plain[p], (unsigned)((N + 127) / 128), 1, 1, 128, 1, 1, 0u,
+                                       (CUstream)st, a, nullptr);
     if (r != CUDA_SUCCESS) return bfail(CUSADI_E_CUDA, "cuLaunchKernel failed: " + std::to_string(r));
   }
   return CUSADI_OK;

@@ -98,6 +98,24 @@ struct Gen {
   bool leaf(int32_t i) const { return g.nodes[i].op == INPUT || g.nodes[i].op == CONST; }
 };
 
+// Whether op is inlined at its uses (else one out-of-line function per op and
+// precision, called from every use).
+bool inlined(int op, int inline_math) {
+  if (inline_math == 1) return true;
+  if (inline_math == 2) return op == EXP || op == EXPM1 || op == LOG || op == LOG1P;
+  return false;
+}
+
+// __launch_bounds__ of a kernel of `threads` threads per CTA: a register cap
+// becomes the minimum number of resident CTAs per SM that leaves each thread
+// at most that many registers (a plain --maxrregcount is ignored for kernels
+// with launch bounds).
+std::string launch_bounds(int threads, int maxrregcount) {
+  std::string s = "__launch_bounds__(" + std::to_string(threads);
+  if (maxrregcount > 0) s += ", " + std::to_string(std::max(1, 65536 / (threads * maxrregcount)));
+  return s + ")";
+}
+
 std::string call_name(int op, bool f64, bool inl) {
   MathFn m = math_name(op);
   if (inl) return f64 ? m.d : m.f;
@@ -232,12 +250,13 @@ std::string op_expr(Gen& G, const Node& x, bool f, const std::string& A, const s
     case OR: e = "((" + A + " != " + Z + " || " + B + " != " + Z + ") ? " + One + " : " + Z + ")"; break;
     case SIGN: e = "(" + A + " > " + Z + " ? " + One + " : (" + A + " < " + Z + " ? -" + One + " : " + Z + "))"; break;
     default:
-      if (!f && !o.inline_math && o.own_math && own_f32_math(x.op)) {
+      if (!f && o.inline_math != 1 && o.own_math && own_f32_math(x.op)) {
         G.own_f32 = true;
         e = std::string(x.op == SIN ? "cs_own_sin_f(" : (x.op == COS ? "cs_own_cos_f(" : "cs_own_exp_f(")) + A + ")";
       } else if (op_call(x.op)) {
-        G.calls.insert({x.op, f});
-        e = call_name(x.op, f, o.inline_math) + "(" + A + (op_arity(x.op) == 2 ? ", " + B : "") + ")";
+        const bool inl = inlined(x.op, o.inline_math);
+        if (!inl) G.calls.insert({x.op, f});
+        e = call_name(x.op, f, inl) + "(" + A + (op_arity(x.op) == 2 ? ", " + B : "") + ")";
       } else {
         e = "/* unsupported op */ " + Z;
       }
@@ -464,7 +483,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     if (NL > 1) src << kLaneAccess;
     if (G.own_f32) src << own_math_source(o.own_math);
     if (o.debug_checks && !o.device_fn) src << "__device__ unsigned int cs_dbg;   // non-finite results\n";
-    if (!o.inline_math) {
+    {
       for (auto& c : G.calls) {
         MathFn m = math_name(c.first);
         const char* t = c.second ? "double" : "float";
@@ -497,7 +516,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
       R.segs.push_back(std::move(S));
       continue;
     }
-    src << "extern \"C\" __global__ void __launch_bounds__(" << o.block << ") " << name << "(\n"
+    src << "extern \"C\" __global__ void " << launch_bounds(o.block, o.maxrregcount) << " " << name << "(\n"
         << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
         << "* __restrict__ X2, long long ldx2, " << tin
         << "* __restrict__ Y, long long ldy,\n    long long N, " << tw
@@ -802,7 +821,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
         << " warps per 32 instances, " << (segs[s].second - segs[s].first) << " phases\n";
     if (G.own_f32) src << own_math_source(o.own_math);
     if (o.debug_checks && !o.device_fn) src << "__device__ unsigned int cs_dbg;   // non-finite results\n";
-    if (!o.inline_math) {
+    {
       for (auto& c : G.calls) {
         MathFn m = math_name(c.first);
         const char* t = c.second ? "double" : "float";
@@ -841,7 +860,7 @@ CodegenResult generate_coop(const Graph& g, const CodegenOptions& o, const CoopP
     }
     // NG groups of 32 instances per CTA: warp w of every group runs role w % W
     // on group w / W, each group with its own block of shared slots
-    src << "extern \"C\" __global__ void __launch_bounds__(" << 32 * W * NG << ") " << name << "(\n"
+    src << "extern \"C\" __global__ void " << launch_bounds(32 * W * NG, o.maxrregcount) << " " << name << "(\n"
         << "    const " << tin << "* __restrict__ X, long long ldx, const " << tin
         << "* __restrict__ X2, long long ldx2, " << tin << "* __restrict__ Y, long long ldy,\n    long long N, "
         << tw << "* __restrict__ W, long long ldw, int acc, int reduce, int vec) {\n"

@@ -107,7 +107,9 @@ struct CodegenOptions {
   int dtype = CUSADI_F64;
   int block = 128;
   int64_t segment_ops = 40000;
-  bool inline_math = false;
+  int inline_math = 0;           // 1: inline every math function; 2: inline the short
+                                 // ones (exp, expm1, log, log1p), call the rest
+  int maxrregcount = 0;          // > 0: registers per thread the launch bounds allow
   int own_math = 0;              // own FP32 sin/cos/exp instead of library calls:
                                  // 1 inlined, 2 out-of-line functions
   int inst_per_thread = 1;       // one-thread kernels: R consecutive instances per thread
@@ -153,29 +155,32 @@ struct InterpProgram {
   std::vector<IOp> ops;
   std::vector<double> k;
   std::vector<uint8_t> in_bcast;
-  int64_t n_slots = 0;
+  int64_t n_slots = 0;             // n_shared + n_global (at least 1)
+  int64_t n_shared = 0;            // slots 0 .. n_shared - 1: shared memory
+  int64_t n_global = 0;            // slots n_shared ..: rows of the global workspace
   bool has_reduce = false;
   std::vector<int64_t> reduce_rows;   // output rows summed over instances (adjoint)
 };
 
-bool pack_interp(const Graph& g, InterpProgram& p, std::string& err);
+// At most max_shared slots go to shared memory (interp.cpp: linear scan).
+bool pack_interp(const Graph& g, InterpProgram& p, std::string& err, int64_t max_shared);
+// Shared-memory slots per thread of the interpreter kernel for a budget in KB.
+int interp_shared_slots(int dtype, int shared_kb);
 
 // launchers implemented in kernels.cu.  Input rows >= split are read from X2
 // (row - split); returns a cudaError_t value.
 int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, const void* X,
                   int64_t ldx, const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy,
-                  int64_t N, void* W, int64_t ldw, int64_t n_slots, int acc, int reduce,
+                  int64_t N, void* W, int64_t ldw, int64_t n_shared, int acc, int reduce,
                   void* Wr, int64_t ldr, void* stream);
 // fixed-order sums of the reduced rows' per-instance terms (row k of Wr, k <
 // n_rows) into column 0 of output rows rows[k]
 int launch_reduce_finish(int dtype, const void* Wr, int64_t ldr, int64_t N, const int64_t* rows,
                          int64_t n_rows, void* Y, int64_t ldy, int accumulate, void* stream);
-// threads per block of the shared-memory interpreter (0: work vector too long)
 // S[r] (+)= sum over the N instances of row r of Y, rows 0..rows-1, in a fixed
 // order; dtype CUSADI_F64 sums doubles, otherwise floats.
 int launch_sum_rows(int dtype, const void* Y, int64_t ldy, int64_t rows, int64_t N, void* S,
                     int accumulate, void* stream);
-int interp_block(int64_t n_slots, int dtype);
 // dense copy of one output argument (kernels.cu); returns a cudaError_t value
 int launch_densify(int dtype, const void* y, int64_t ldy, int64_t off, const int32_t* map,
                    int64_t n_dense, void* dense, int64_t ldd, int64_t N, int sms, void* stream);

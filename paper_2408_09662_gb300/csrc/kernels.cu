@@ -16,6 +16,8 @@
 namespace cusadi {
 namespace {
 
+constexpr int kInterpBlock = 128;   // threads per CTA of the interpreter kernel
+
 template <typename T>
 __device__ __forceinline__ T eval_op(uint32_t op, T a, T b, T k) {
   const T Z = T(0), O = T(1);
@@ -68,42 +70,49 @@ __device__ __forceinline__ T eval_op(uint32_t op, T a, T b, T k) {
 }
 
 // B: buffer element type; S: work-slot type; MIXED: per-op precision tags.
-template <typename B, typename S, bool MIXED, bool SMEM>
-__global__ void __launch_bounds__(256) interp_kernel(
+// Slots below n_shared live in shared memory (slot-major, one column per
+// thread: conflict-free), the others in the global workspace (row s - n_shared,
+// instance-fastest); every slot index in the stream is warp-uniform, so the
+// tier test never diverges.
+template <typename B, typename S, bool MIXED>
+__global__ void __launch_bounds__(kInterpBlock) interp_kernel(
     const uint4* __restrict__ ops, long long n_ops, const double* __restrict__ K,
     const B* __restrict__ X, long long ldx, const B* __restrict__ X2, long long ldx2,
     long long split, B* __restrict__ Y, long long ldy, long long N, S* __restrict__ W,
-    long long ldw, int acc, int reduce, S* __restrict__ Wr, long long ldr) {
+    long long ldw, unsigned n_shared, int acc, int reduce, S* __restrict__ Wr, long long ldr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i0 < N;
   const long long ix = active ? i0 : N - 1;  // inactive lanes read a valid column
-  S* w = SMEM ? reinterpret_cast<S*>(smem_raw) + threadIdx.x : W + i0;
-  const long long ws = SMEM ? (long long)blockDim.x : ldw;
+  S* const sm = reinterpret_cast<S*>(smem_raw) + threadIdx.x;
+  S* const gm = W + i0;                      // columns up to the grid's end exist (ldw)
+  auto at = [&](unsigned s) -> S& {
+    return s < n_shared ? sm[(size_t)s * kInterpBlock] : gm[(long long)(s - n_shared) * ldw];
+  };
   for (long long t = 0; t < n_ops; ++t) {
     const uint4 o = __ldg(&ops[t]);
     const uint32_t op = o.x & 127u;
     const long long aux = (long long)(o.x >> 8);
     if (op == INPUT) {
       const long long col = o.w ? 0 : ix;
-      w[o.y * ws] = aux < split ? (S)X[aux * ldx + col] : (S)X2[(aux - split) * ldx2 + col];
+      at(o.y) = aux < split ? (S)X[aux * ldx + col] : (S)X2[(aux - split) * ldx2 + col];
       continue;
     }
     if (op == CONST) {
-      w[o.y * ws] = (S)K[aux];
+      at(o.y) = (S)K[aux];
       continue;
     }
     if (op == OUTPUT) {
-      B v = (B)w[o.z * ws];
+      const S v = at(o.z);
       if (o.w && reduce) {   // reduced row o.w - 1: the instance's term, summed later
-        if (active) Wr[(long long)(o.w - 1) * ldr + i0] = w[o.z * ws];
+        if (active) Wr[(long long)(o.w - 1) * ldr + i0] = v;
       } else if (active) {
         B* p = &Y[aux * ldy + i0];
-        *p = acc ? *p + v : v;
+        *p = acc ? *p + (B)v : (B)v;
       }
       continue;
     }
-    const S a = w[o.z * ws], b = w[o.w * ws];
+    const S a = at(o.z), b = at(o.w);
     const double kd = op == FMA_CONST ? K[aux] : 0.0;
     S r;
     if (!MIXED || ((o.x >> 7) & 1u)) {
@@ -111,25 +120,26 @@ __global__ void __launch_bounds__(256) interp_kernel(
     } else {
       r = (S)eval_op<float>(op, (float)a, (float)b, (float)kd);
     }
-    w[o.y * ws] = r;
+    at(o.y) = r;
   }
 }
 
-template <typename B, typename S, bool MIXED, bool SMEM>
+template <typename B, typename S, bool MIXED>
 int launch(const IOp* ops, int64_t n_ops, const double* k, const void* X, int64_t ldx,
            const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy, int64_t N, void* W,
-           int64_t ldw, int64_t n_slots, int block, int acc, int reduce, void* Wr, int64_t ldr,
+           int64_t ldw, int64_t n_shared, int acc, int reduce, void* Wr, int64_t ldr,
            cudaStream_t st) {
-  auto kern = interp_kernel<B, S, MIXED, SMEM>;
-  size_t smem = SMEM ? (size_t)n_slots * block * sizeof(S) : 0;
+  auto kern = interp_kernel<B, S, MIXED>;
+  size_t smem = (size_t)n_shared * kInterpBlock * sizeof(S);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
   }
-  long long grid = (N + block - 1) / block;
-  kern<<<(unsigned)grid, block, smem, st>>>(reinterpret_cast<const uint4*>(ops), n_ops, k,
-                                            (const B*)X, ldx, (const B*)X2, ldx2, split, (B*)Y,
-                                            ldy, N, (S*)W, ldw, acc, reduce, (S*)Wr, ldr);
+  long long grid = (N + kInterpBlock - 1) / kInterpBlock;
+  kern<<<(unsigned)grid, kInterpBlock, smem, st>>>(reinterpret_cast<const uint4*>(ops), n_ops, k,
+                                                    (const B*)X, ldx, (const B*)X2, ldx2, split, (B*)Y,
+                                                    ldy, N, (S*)W, ldw, (unsigned)n_shared, acc, reduce,
+                                                    (S*)Wr, ldr);
   return (int)cudaGetLastError();
 }
 
@@ -176,31 +186,21 @@ __global__ void __launch_bounds__(512) sum_rows_kernel(const T* __restrict__ Y, 
 
 }  // namespace
 
-// Threads per block for the shared-memory work vector (0: it does not fit).
-int interp_block(int64_t n_slots, int dtype) {
+int interp_shared_slots(int dtype, int shared_kb) {
   const size_t elt = dtype == CUSADI_F32 ? 4 : 8;
-  const size_t budget = 200 * 1024;
-  for (int b = 128; b >= 32; b -= 32)
-    if ((size_t)n_slots * b * elt <= budget) return b;
-  return 0;
+  return (int)(((size_t)std::max(0, shared_kb) * 1024) / (kInterpBlock * elt));
 }
 
 int launch_interp(const IOp* ops, int64_t n_ops, const double* k, int dtype, const void* X,
                   int64_t ldx, const void* X2, int64_t ldx2, int64_t split, void* Y, int64_t ldy,
-                  int64_t N, void* W, int64_t ldw, int64_t n_slots, int acc, int reduce,
+                  int64_t N, void* W, int64_t ldw, int64_t n_shared, int acc, int reduce,
                   void* Wr, int64_t ldr, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  int b = interp_block(n_slots, dtype);
-  const bool smem = b > 0;
-  if (!smem) b = 128;
   if (dtype == CUSADI_F64)
-    return smem ? launch<double, double, false, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st)
-                : launch<double, double, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st);
+    return launch<double, double, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_shared, acc, reduce, Wr, ldr, st);
   if (dtype == CUSADI_F32)
-    return smem ? launch<float, float, false, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st)
-                : launch<float, float, false, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st);
-  return smem ? launch<float, double, true, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st)
-              : launch<float, double, true, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_slots, b, acc, reduce, Wr, ldr, st);
+    return launch<float, float, false>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_shared, acc, reduce, Wr, ldr, st);
+  return launch<float, double, true>(ops, n_ops, k, X, ldx, X2, ldx2, split, Y, ldy, N, W, ldw, n_shared, acc, reduce, Wr, ldr, st);
 }
 
 // Dense copy of one sparse output argument: dense[k * ldd + i] = y[(off +

@@ -216,7 +216,8 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.dtype = fn->opt.dtype;
   co.block = fn->opt.block;
   co.segment_ops = fn->opt.segment_ops;
-  co.inline_math = fn->opt.inline_math != 0;
+  co.inline_math = fn->opt.inline_math;
+  co.maxrregcount = fn->opt.maxrregcount;
   co.own_math = fn->opt.own_math;
   co.debug_checks = fn->opt.debug_checks != 0;
   co.inst_per_thread = fn->opt.ways > 1 ? 1 : fn->opt.inst_per_thread;
@@ -280,7 +281,8 @@ cusadi_status prepare_direction(cusadi_fn fn, Direction& d, bool adjoint) {
     fn->path = CUSADI_PATH_INTERP;
   }
   std::string err;
-  if (!pack_interp(d.g, d.ip, err)) return fail(CUSADI_E_UNSUPPORTED, err);
+  if (!pack_interp(d.g, d.ip, err, interp_shared_slots(fn->opt.dtype, fn->opt.interp_shared_kb)))
+    return fail(CUSADI_E_UNSUPPORTED, err);
   d.n_slots = d.ip.n_slots;
   return CUSADI_OK;
 }
@@ -383,7 +385,7 @@ int64_t interp_ldw(int64_t N) { return round_up(std::max<int64_t>(N, 1), 128); }
 size_t direction_ws(cusadi_fn fn, const Direction& d, int64_t N) {
   if (N <= 0) return 0;
   if (fn->path == CUSADI_PATH_INTERP)   // global work slots (if any), then reduced-row terms
-    return ((interp_block(d.ip.n_slots, fn->opt.dtype) > 0 ? 0 : (size_t)d.ip.n_slots * interp_ldw(N)) +
+    return ((size_t)d.ip.n_global * interp_ldw(N) +
             d.ip.reduce_rows.size() * (size_t)round_up(N, 32)) * elt_ws(fn->opt.dtype);
   // rows carried between kernels, then (adjoint) one row of per-instance terms per reduced row
   return ((size_t)d.cg.ws_rows + d.cg.reduce_rows.size()) * round_up(N, 32) * elt_ws(fn->opt.dtype);
@@ -403,13 +405,13 @@ cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const 
   if (fn->path == CUSADI_PATH_INTERP) {
     const int64_t lw = ldw > 0 ? ldw : interp_ldw(N);
     void* Wr = (W && !d.ip.reduce_rows.empty())
-                   ? (void*)((char*)W + (interp_block(d.ip.n_slots, fn->opt.dtype) > 0 ? 0 : (size_t)d.ip.n_slots * lw) *
+                   ? (void*)((char*)W + (size_t)d.ip.n_global * lw *
                                             elt_ws(fn->opt.dtype))
                    : nullptr;
     int rc = launch_interp((const IOp*)(adjoint ? ds.d_ops_adj : ds.d_ops_fwd),
                            (int64_t)d.ip.ops.size(), adjoint ? ds.d_k_adj : ds.d_k_fwd,
                            fn->opt.dtype, X, ldx, X2 ? X2 : X, ldx2, adjoint ? fn->ir.nnz_in : (int64_t)1 << 40,
-                           Y, ldy, N, W, lw, d.ip.n_slots, acc, reduce, Wr, round_up(N, 32), stream);
+                           Y, ldy, N, W, lw, d.ip.n_shared, acc, reduce, Wr, round_up(N, 32), stream);
     if (rc != 0) return fail(CUSADI_E_CUDA, std::string("interpreter launch: ") + cudaGetErrorString((cudaError_t)rc));
     return CUSADI_OK;
   }
@@ -521,6 +523,7 @@ void cusadi_default_options(cusadi_options* o) {
   o->inst_per_thread = 1;
   o->coop_groups = 1;
   o->sync_every = 0;
+  o->interp_shared_kb = 96;
   o->cache_dir = nullptr;
 }
 
@@ -562,6 +565,7 @@ cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* o
   if (o.compile_limit_ops <= 0) o.compile_limit_ops = 300000;
   if (o.ways < 0 || o.ways > 16 || o.ways == 1) return fail(CUSADI_E_INVALID_ARG, "ways must be 0 or 2..16");
   if (o.own_math < 0 || o.own_math > 2) return fail(CUSADI_E_INVALID_ARG, "own_math must be 0, 1 or 2");
+  if (o.inline_math < 0 || o.inline_math > 2) return fail(CUSADI_E_INVALID_ARG, "inline_math must be 0, 1 or 2");
   if (o.inst_per_thread <= 0) o.inst_per_thread = 1;
   if (o.inst_per_thread != 1 && o.inst_per_thread != 2 && o.inst_per_thread != 4)
     return fail(CUSADI_E_INVALID_ARG, "inst_per_thread must be 1, 2 or 4");
@@ -570,6 +574,8 @@ cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* o
   if (o.ways > 1 && 32 * o.ways * o.coop_groups > 1024)
     return fail(CUSADI_E_INVALID_ARG, "32 * ways * coop_groups must not exceed 1024 threads");
   if (o.sync_every < 0) return fail(CUSADI_E_INVALID_ARG, "sync_every must be >= 0");
+  if (o.interp_shared_kb < 0 || o.interp_shared_kb > 200)
+    return fail(CUSADI_E_INVALID_ARG, "interp_shared_kb must be in [0, 200]");
   if (o.cache_dir) fn->cache_dir = o.cache_dir;
   o.cache_dir = nullptr;  // the caller's string is not kept
   auto t0 = std::chrono::steady_clock::now();
@@ -918,7 +924,7 @@ cusadi_status adjoint_impl(cusadi_fn fn, const void* in, int64_t ld_in, const vo
   // sum them in a fixed order (the same bits on every run)
   if (fn->path == CUSADI_PATH_INTERP) {
     const InterpProgram& ip = fn->adj.ip;
-    const size_t off = (interp_block(ip.n_slots, fn->opt.dtype) > 0 ? 0 : (size_t)ip.n_slots * interp_ldw(N)) *
+    const size_t off = (size_t)ip.n_global * interp_ldw(N) *
                        elt_ws(fn->opt.dtype);
     int rc = launch_reduce_finish(fn->opt.dtype, (char*)workspace + off, round_up(N, 32), N, ds->d_reduce_rows,
                                   (int64_t)ip.reduce_rows.size(), sum_dst, sum_ld, acc_bcast ? 1 : 0,

@@ -146,3 +146,26 @@ def roofline_seconds(fn, f64_peaks: dict, f32_peaks: dict, adjoint: bool = False
     c32 = [a - b for a, b in zip(counts, c64)]
     return (weighted_ops(c64, f64_peaks["weights"]) / f64_peaks["fma_per_s"] +
             weighted_ops(c32, f32_peaks["weights"]) / f32_peaks["fma_per_s"])
+
+
+def sustained_fma(dtype: str, seconds: float = 1.5) -> float:
+    """FMA/s of the FMA-chain kernel launched back to back for about `seconds`
+    (one CUDA-event interval around all launches): the rate under the power
+    draw of a full FMA load, which a clock sampler can watch."""
+    props = torch.cuda.get_device_properties(0)
+    N = props.multi_processor_count * 2048 * 4
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    rng = np.random.default_rng(0)
+    x = torch.tensor(np.vstack([rng.uniform(0.5, 1.5, (CHAINS, N)),
+                                rng.uniform(1.0, 2.0, (CHAINS, N))]), dtype=tdt, device="cuda")
+    fn = Function(_chain_program("fma"), dtype=dtype, schedule=0, inline_math=1)
+    per_launch = _time(fn, x)
+    reps = max(1, int(seconds / per_launch))
+    y = fn(x)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn(x, out=y)
+    e.record()
+    e.synchronize()
+    return fn.info.n_ops * N * reps / (s.elapsed_time(e) * 1e-3)

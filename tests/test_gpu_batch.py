@@ -83,42 +83,51 @@ def test_tune_picks_a_tile_size(batch):
     assert blk in (32, 64, 128) and b.info()["block"] == blk and b.info()["grid"] > 0
 
 
-COOP_SIZES = [(70000, 200), (3000, 2000), (500, 5000)]
+COOP_SIZES = [(70000, 200), (3000, 2000), (500, 5000), (45000, 4099)]
 
 
-def test_cooperative_tiles_equal_plain_launches():
-    """ways=4: the 70k-op program (few instances, many ops) runs as cooperative
-    tiles: the 128-thread scheduler's 4 warps split one group of 32 instances,
-    and its per-program launch runs the same cooperative code.  With FMA
-    contraction off every op rounds once in any layout, so the persistent
-    launch, the plain launches and the standalone one-thread-per-instance
-    kernel agree bit for bit; 32- and 64-thread tiles are refused.  The 70k-op
-    random program is too deep to compare with the oracle (two correct FP64
-    evaluations of it drift apart by O(1) in its last outputs); the regular
-    programs meet the FP64 rule against the oracle."""
+@pytest.mark.parametrize("ways", [4, 8])
+def test_satellites_equal_plain_launches(ways):
+    """ways = W: the 70k- and 45k-op programs (few instances, many ops) run as
+    satellite kernels, W warps splitting each group of 32 instances, beside
+    the persistent kernel of the others; the plain mode launches the same
+    kernels.  With FMA contraction off every op rounds once in any layout, so
+    the persistent launch, the plain launches and the standalone
+    one-thread-per-instance kernel agree bit for bit, for every tile size and
+    after the buffers change (the satellites' graph branches are captured
+    again).  The 70k-op random program is too deep for the FP64 parity rule
+    (two correct FP64 evaluations of it drift apart by O(1) in its last
+    outputs); the others meet it against the oracle."""
     irs = [programs.random_program(n, seed=300 + j).to_bytes() for j, (n, _) in enumerate(COOP_SIZES)]
-    b = Batch(irs, [N for _, N in COOP_SIZES], dtype="f64", ways=4, fmad=0)
+    b = Batch(irs, [N for _, N in COOP_SIZES], dtype="f64", ways=ways, fmad=0)
     xn = [inputs.normal(64, N, seed=400 + j) for j, (_, N) in enumerate(COOP_SIZES)]
     xs = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in xn]
     outs = [torch.full((32, N), float("nan"), dtype=torch.float64, device="cuda") for _, N in COOP_SIZES]
     b(xs, outs, mode="plain")
     torch.cuda.synchronize()
     plain = [o.cpu().numpy() for o in outs]
-    with pytest.raises(Exception):
-        b.set_block(32)
-    for _ in range(2):
-        for o in outs:
-            o.fill_(float("nan"))
-        b(xs, outs, mode="persistent")
-        torch.cuda.synchronize()
-        for j in range(len(COOP_SIZES)):
-            np.testing.assert_array_equal(outs[j].cpu().numpy(), plain[j], err_msg=f"program {j}")
-    alone = Function(irs[0], dtype="f64", fmad=0)(xs[0])
+    for block in (32, 64, 128):
+        b.set_block(block)
+        for _ in range(2):
+            for o in outs:
+                o.fill_(float("nan"))
+            b(xs, outs, mode="persistent")
+            torch.cuda.synchronize()
+            for j in range(len(COOP_SIZES)):
+                np.testing.assert_array_equal(outs[j].cpu().numpy(), plain[j], err_msg=f"program {j}")
+    outs2 = [torch.zeros_like(o) for o in outs]          # new buffers: graph captured again
+    b(xs, outs2)
     torch.cuda.synchronize()
-    np.testing.assert_array_equal(plain[0], alone.cpu().numpy())
-    for j in (1, 2):
+    for j in range(len(COOP_SIZES)):
+        np.testing.assert_array_equal(outs2[j].cpu().numpy(), plain[j], err_msg=f"program {j}")
+    for j in (0, 3):
+        alone = Function(irs[j], dtype="f64", fmad=0)(xs[j])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(plain[j], alone.cpu().numpy())
+    for j in (1, 2, 3):
         orc = Oracle(irs[j])
-        idx = np.random.default_rng(j).choice(COOP_SIZES[j][1], 40, replace=False)
+        idx = np.unique(np.r_[np.random.default_rng(j).choice(COOP_SIZES[j][1], 40, replace=False),
+                              COOP_SIZES[j][1] - 1])
         ref = orc.eval(xn[j][:, idx])
         tol = tolerance(orc, xn[j][:, idx], ref, 1e-12, kind=0)
         assert np.all(np.abs(plain[j][:, idx] - ref) <= tol)
@@ -131,8 +140,9 @@ C5_SIZES = [(1000, 65536), (5000, 32768), (10000, 32768), (20000, 16384), (50000
 
 
 def test_uneven_batch_at_stated_sizes_against_the_oracle():
-    """FP32, one persistent launch with cooperative tiles for the longest
-    programs (ways = 4), every program at its stated instance count.  Sampled
+    """FP32, one persistent launch with the 50k- to 200k-op programs as
+    satellite kernels (8 warps per group), every program at its stated
+    instance count.  Sampled
     instances (64 per program plus the last, ragged, one) against the FP64
     oracle under the FP32 rule max(2e-4 s_k, 2 B32_k,i, 4 S_k): B32 is the
     first-order rounding bound, S_k the largest deviation of 8 Monte Carlo
@@ -141,7 +151,7 @@ def test_uneven_batch_at_stated_sizes_against_the_oracle():
     the fraction of outputs within the plain 2e-4 s_k is recorded and must
     fall with depth as the oracle says it does."""
     irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(C5_SIZES)]
-    b = Batch(irs, [N for _, N in C5_SIZES], dtype="f32", ways=4)
+    b = Batch(irs, [N for _, N in C5_SIZES], dtype="f32", ways=8)
     xn = [inputs.normal(64, N, seed=200 + j).astype(np.float32).astype(np.float64)
           for j, (_, N) in enumerate(C5_SIZES)]
     xs = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in xn]

@@ -393,10 +393,29 @@ def test_cooperative_kernels_reach_every_barrier(ways, shared_kb, monkeypatch):
 
 
 def test_batch_ways_validated():
-    o = _opt(ways=2)
-    with pytest.raises(L.CusadiError) as e:
-        L.cusadi_batch_create([programs.listing2().to_bytes()], [16], o)
-    assert e.value.status == L.CUSADI_E_INVALID_ARG
+    for w in (1, 17, -1):
+        with pytest.raises(L.CusadiError) as e:
+            L.cusadi_batch_create([programs.listing2().to_bytes()], [16], _opt(ways=w))
+        assert e.value.status == L.CUSADI_E_INVALID_ARG
+
+
+def test_batch_satellites_compile_and_leave_the_scheduler():
+    """A long program with few instances becomes a satellite under ways > 1:
+    its instances leave the scheduler's tile table."""
+    irs = [programs.random_program(n, seed=110 + j).to_bytes() for j, n in enumerate([400, 40000])]
+    o = _opt(dtype=L.CUSADI_F32, segment_ops=9000, ways=8)
+    b = L.cusadi_batch_create(irs, [1000, 300], o)
+    try:
+        n_tiles, block, _, _ = L.cusadi_batch_info(b)
+        assert block == 128 and n_tiles == 8            # program 0 only: 1000 / 128
+        assert L.cusadi_batch_op_counts(b, 1)[Op.ADD] > 0
+    finally:
+        L.cusadi_batch_free(b)
+    b = L.cusadi_batch_create(irs, [1000, 300], _opt(dtype=L.CUSADI_F32, segment_ops=9000))
+    try:
+        assert L.cusadi_batch_info(b)[0] == 8 + 3        # no satellites without ways
+    finally:
+        L.cusadi_batch_free(b)
 
 
 def test_cooperative_ways_validated():
