@@ -203,10 +203,11 @@ def other_configs(dev, pk64, pk32, flush, reps, oracle_check=True):
     def make_batch():
         t0 = time.perf_counter()
         irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(sizes)]
-        # ways=8: programs with few instances and many ops (here the 50k-200k-op
-        # ones) run as satellite kernels, 8 warps per group of 32 instances,
-        # beside the persistent kernel of the others
-        return Batch(irs, [N for _, N in sizes], dtype="f32", ways=8), time.perf_counter() - t0, irs
+        # ways=4: programs with few instances and many ops (here the 50k-200k-op
+        # ones) run as satellite kernels, 4 warps per group of 32 instances,
+        # beside the persistent kernel of the others (4 measured faster than 8
+        # and 16 for this batch and for each of those programs alone)
+        return Batch(irs, [N for _, N in sizes], dtype="f32", ways=4), time.perf_counter() - t0, irs
     ir3 = programs.quadrotor_mpc().to_bytes()
     ir1 = programs.quadrotor_lqr_step().to_bytes()
     srb = programs.srb_step().to_bytes()
@@ -242,6 +243,17 @@ def other_configs(dev, pk64, pk32, flush, reps, oracle_check=True):
     ms = _events_ms(lambda: c1w(x, out=y), reps, flush)
     rec["N4096_ways4"] = {"ms": ms, "instance_evals_per_s": 4096 / (ms * 1e-3),
                           "frac_of_measured_fma_f64": frac(c1w, 4096, ms, "f64")}
+    # the autotuner's launch at both batch sizes (a short program: its candidates compile in
+    # well under a second each)
+    from paper_2408_09662_gb300.tune import autotune
+    for N in (4096, 65536):
+        x = torch.tensor(inputs.cartpole(N, seed=0), device=dev)
+        fa = autotune(ir_c1, x, "f64", use_cache=False)
+        y = fa(x)
+        ms = _events_ms(lambda: fa(x, out=y), reps, flush)
+        rec[f"N{N}_tuned"] = {"launch": fa.tune_record["options"], "ms": ms,
+                              "instance_evals_per_s": N / (ms * 1e-3),
+                              "frac_of_measured_fma_f64": frac(fa, N, ms, "f64")}
     out["cartpole_rk4_jacobian_f64"] = rec
 
     # --- C3 closed-form MPC, N = 16384, all-FP64 vs mixed (FP32 bulk, FP64 pivots) ---
@@ -377,9 +389,9 @@ def other_configs(dev, pk64, pk32, flush, reps, oracle_check=True):
         "op_instances_generated": gen_ops, "persistent_ms": ms_p, "plain_8_launches_ms": ms_s,
         "speedup_persistent_vs_plain": ms_s / ms_p, "tile_block": block,
         "persistent_ms_by_tile_block": {str(k): v for k, v in by_block.items()},
-        "satellites": "ways=8: programs with N <= 8192 and >= 20,000 ops after the passes (here the "
+        "satellites": "ways=4: programs with N <= 8192 and >= 20,000 ops after the passes (here the "
                       "50k-, 100k-, 150k- and 200k-op ones) run as cooperative kernels of their own, "
-                      "8 warps per group of 32 instances, on parallel graph branches beside the "
+                      "4 warps per group of 32 instances, on parallel graph branches beside the "
                       "persistent kernel of the other four; their plain launch runs the same kernels",
         **b.info(),
         "gop_per_s_generated": gen_ops / (ms_p * 1e-3) * 1e-9, "setup_seconds": t_compile}
@@ -433,6 +445,10 @@ def run_experiment(name):
         experiments.mpc_pareto()
     elif name == "roa":
         experiments.lqr_roa()
+    elif name == "batch":
+        experiments.batch_sweep()
+    elif name == "interp":
+        experiments.interp_sweep()
     else:
         from oracle import Oracle
         cores = os.cpu_count() or 1
@@ -465,8 +481,13 @@ def main():
     ap.add_argument("--ways64", default="auto",
                     help="warps per 32 instances of the FP64 kernel: auto (faster of 0, 4), or a number")
     ap.add_argument("--ways32", default="auto",
-                    help="warps per 32 instances of the FP32 kernel: auto (fastest of 0, 2, 4, 8), or a number")
-    ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc", "roa"],
+                    help="warps per 32 instances of the FP32 kernel: auto (fastest of 0, 4, 8), or a number")
+    ap.add_argument("--launch64", default=None,
+                    help='fixed launch options of the FP64 kernel as JSON (e.g. \'{"ways": 4, '
+                         '"coop_groups": 2}\'): no tuning')
+    ap.add_argument("--launch32", default=None,
+                    help="fixed launch options of the FP32 kernel as JSON: no tuning")
+    ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc", "roa", "batch", "interp"],
                     help="run one of the paper's experiments instead (markdown table, no JSON line); "
                          "ldlt adds the CPU oracle as its CPU baseline column")
     args = ap.parse_args()
@@ -493,6 +514,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2408_09662_gb300 import inputs, peaks, programs
+    from paper_2408_09662_gb300.api import Function
     from paper_2408_09662_gb300.tune import autotune
 
     ir = programs.random_program(N_OPS_GEN, seed=PROGRAM_SEED).to_bytes()
@@ -506,8 +528,15 @@ def main():
     # on one box and 11.0-11.1 ms on others, so only the steady shapes compete.
     cand = {"f64": (0, 4) if args.ways64 == "auto" else (int(args.ways64),),
             "f32": (0, 4, 8) if args.ways32 == "auto" else (int(args.ways32),)}
-    fn64 = autotune(ir, x64, "f64", ways=cand["f64"], use_cache=False)   # one after the other:
-    fn32 = autotune(ir, x32, "f32", ways=cand["f32"], use_cache=False)   # nothing else on the GPU
+    def launch(dt, fixed, x):
+        if fixed is not None:
+            opts = json.loads(fixed)
+            fn = Function(ir, dtype=dt, **opts)
+            fn.tune_record = {"options": opts, "candidates": [], "fixed": True}
+            return fn
+        return autotune(ir, x, dt, ways=cand[dt], use_cache=False)
+    fn64 = launch("f64", args.launch64, x64)      # one after the other:
+    fn32 = launch("f32", args.launch32, x32)      # nothing else on the GPU
     tuning = {dt: {"chosen": fn.tune_record["options"],
                    "candidates_ms": [[json.dumps(o, sort_keys=True), ms] for o, ms in fn.tune_record["candidates"]]}
               for dt, fn in (("f64", fn64), ("f32", fn32))}

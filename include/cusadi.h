@@ -114,7 +114,9 @@ typedef struct {
   int32_t interp_shared_kb;   /* interpreter path: shared memory per 128-thread CTA for the
                                  work slots, in KB (0..200); the slots of the values that
                                  do not fit, chosen by linear scan as the ones read
-                                 last, live in the workspace                       (96) */
+                                 last, live in the workspace; more shared memory
+                                 means fewer resident CTAs, which costs more than the
+                                 slots gain beyond ~48 KB on GB300                 (48) */
   const char* cache_dir;      /* directory for compiled kernels, NULL = in-memory only */
 } cusadi_options;
 

@@ -523,7 +523,7 @@ void cusadi_default_options(cusadi_options* o) {
   o->inst_per_thread = 1;
   o->coop_groups = 1;
   o->sync_every = 0;
-  o->interp_shared_kb = 96;
+  o->interp_shared_kb = 48;
   o->cache_dir = nullptr;
 }
 

@@ -5,6 +5,8 @@ markdown table.
     python -m paper_2408_09662_gb300.experiments coop   # within-instance parallelism (§VI)
     python -m paper_2408_09662_gb300.experiments roa    # LQR quadcopter region of attraction (§V-C)
     python -m paper_2408_09662_gb300.experiments mpc    # MPC cost/violation vs iterations (§V-A, Fig. 4)
+    python -m paper_2408_09662_gb300.experiments batch  # uneven batch: satellite widths
+    python -m paper_2408_09662_gb300.experiments interp # interpreter vs compiled (LDL^T family)
     python -m paper_2408_09662_gb300.experiments one random20k f64 4096 8   # one kernel, for a profiler
     python -m paper_2408_09662_gb300.experiments one srb f64 65536 0 adjoint
 
@@ -245,6 +247,73 @@ def lqr_roa(N=10000, steps=250, u_maxes=(6.0, 8.0, 10.0, 15.0, 20.0), seed=3, dt
     return rows
 
 
+UNEVEN_BATCH = [(1000, 65536), (5000, 32768), (10000, 32768), (20000, 16384), (50000, 8192),
+                (100000, 4096), (150000, 2048), (200000, 512)]
+
+
+def batch_sweep(ways_list=(4, 8, 16), reps=7):
+    """The uneven batch (8 random programs of the 20k-op generator, seeds
+    100..107, FP32) with its long few-instance programs as satellite kernels
+    of W warps per group: persistent graph launch at each tile size, the 8
+    plain launches, and each satellite-sized program alone at each W."""
+    irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(UNEVEN_BATCH)]
+    xs = [torch.tensor(inputs.normal(64, N, seed=200 + j), dtype=torch.float32, device="cuda")
+          for j, (_, N) in enumerate(UNEVEN_BATCH)]
+    outs = [torch.empty((32, N), dtype=torch.float32, device="cuda") for _, N in UNEVEN_BATCH]
+    from .api import Batch
+    print("| satellite ways | setup s | persistent ms (tile 32 / 64 / 128) | 8 plain launches ms |")
+    print("|---|---|---|---|")
+    rows = []
+    for w in ways_list:
+        t0 = time.perf_counter()
+        b = Batch(irs, [N for _, N in UNEVEN_BATCH], dtype="f32", ways=w)
+        setup = time.perf_counter() - t0
+        per = []
+        for blk in (32, 64, 128):
+            b.set_block(blk)
+            per.append(_gpu_ms(lambda: b(xs, outs), reps=reps))
+        plain = _gpu_ms(lambda: b(xs, outs, mode="plain"), reps=reps)
+        rows.append((w, setup, per, plain))
+        print(f"| {w} | {setup:.0f} | {per[0]:.3f} / {per[1]:.3f} / {per[2]:.3f} | {plain:.3f} |", flush=True)
+    print("\n| program | N | ways | ms alone |")
+    print("|---|---|---|---|")
+    for j in range(4, 8):
+        n, N = UNEVEN_BATCH[j]
+        for w in (0,) + tuple(ways_list):
+            fn = Function(irs[j], dtype="f32", ways=w)
+            y = torch.empty((32, N), dtype=torch.float32, device="cuda")
+            ms = _gpu_ms(lambda: fn(xs[j], out=y), reps=reps)
+            rows.append((n, N, w, ms))
+            print(f"| random {n // 1000}k ops | {N} | {w} | {ms:.3f} |", flush=True)
+    return rows
+
+
+def interp_sweep(sizes=(22, 47), N=65536, budgets_kb=(0, 16, 48, 96)):
+    """The interpreter kernel against compiled code on the LDL^T family (FP64):
+    time per op-instance at each shared-memory budget for the work slots,
+    and the workspace the slots beyond it need."""
+    from . import _lib as L
+    print("| n | ops | path | shared KB | ms | ns per op-instance x 1e3 | vs compiled | workspace MB |")
+    print("|---|---|---|---|---|---|---|---|")
+    rows = []
+    for n in sizes:
+        irb = programs.ldlt_spd_solve(n).to_bytes()
+        X = _spd(n, N, seed=n)
+        fns = [("compiled", None, Function(irb, dtype="f64"))] + \
+              [("interp", kb, Function(irb, dtype="f64", path="interp", interp_shared_kb=kb)) for kb in budgets_kb]
+        base = None
+        for path, kb, fn in fns:
+            x = torch.tensor(X, device="cuda")
+            y = torch.empty((fn.nnz_out, N), dtype=torch.float64, device="cuda")
+            ms = _gpu_ms(lambda: fn(x, out=y))
+            base = ms if base is None else base
+            ws = L.cusadi_workspace_bytes(fn.handle, N, False) / 1e6
+            rows.append((n, fn.info.n_ops, path, kb, ms, ws))
+            print(f"| {n} | {fn.info.n_ops} | {path} | {'' if kb is None else kb} | {ms:.3f} | "
+                  f"{ms * 1e9 / (fn.info.n_ops * N):.3f} | {ms / base:.1f}x | {ws:.0f} |", flush=True)
+    return rows
+
+
 def one_kernel(program="random20k", dtype="f64", N=4096, ways=0, reps=3, adjoint=False):
     """Compile one program and launch it `reps` times (a small case for a
     profiler); adjoint: its reverse sweep (broadcast rows reduced) instead."""
@@ -277,6 +346,10 @@ def main(argv):
         mpc_pareto()
     elif which == "roa":
         lqr_roa()
+    elif which == "batch":
+        batch_sweep()
+    elif which == "interp":
+        interp_sweep()
     elif which == "one":
         # one <program> <dtype> <N> <ways> [adjoint]
         prog, dt, N, w = (argv[2:] + ["random20k", "f64", "4096", "0"][len(argv) - 2:])[:4]

@@ -16,11 +16,12 @@ the chosen kernel directly.
 Search, in two rounds:
 1. shape: ways in `ways` (0 = one thread per instance, W = W warps per group
    of 32 instances);
-2. around the best shape of each family (ways = 0 and ways > 0): for ways = 0, instances per thread (2, 4), a CTA
-   barrier every few hundred ops with larger CTAs, and register caps (128, 96,
-   64: measured on GB300, a cap of 128 takes the random 20k-op FP32 kernel from
-   0.61 to 0.37 ms and 64 the cart-pole FP64 kernel from 0.142 to 0.115 ms);
-   for ways > 0, 2 or 4 groups of 32 instances per CTA.
+2. around the best shape of each family (ways = 0 and ways > 0): for ways = 0,
+   instances per thread (2, 4) and register caps (128, 96, 64: measured on
+   GB300, a cap of 128 takes the random 20k-op FP32 kernel from 0.61 to 0.37 ms
+   and 64 the cart-pole FP64 kernel from 0.142 to 0.115 ms); for ways > 0, 2 or
+   4 groups of 32 instances per CTA.  (CTA barriers every few hundred ops,
+   sync_every, measured no faster on any program and are not searched.)
 """
 from __future__ import annotations
 
@@ -45,8 +46,6 @@ def _refinements(best: dict, dtype: str, n_ops: int, n_slots: int) -> list:
     if best.get("ways", 0) == 0:
         regs_per_value = 2 if dtype == "f64" else 1
         out += [dict(best, inst_per_thread=r) for r in (2, 4) if n_slots * r * regs_per_value <= 512]
-        if n_ops >= 2000:   # long kernels: keep each CTA's warps in the same stretch of code
-            out += [dict(best, block=256, sync_every=256), dict(best, block=512, sync_every=1024)]
         # register caps: more resident warps at the price of some spills
         out += [dict(best, maxrregcount=r) for r in (128, 96, 64) if n_slots * regs_per_value > r]
     else:

@@ -210,6 +210,31 @@ def test_rollout_loss_sum_is_bitwise_reproducible(prog64):
     assert Ls[0] == Ls[1] == Ls[2]
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rollout_at_the_benchmark_batch_against_oracle(dtype):
+    """The benchmark's rollout configuration itself: N = 4,096 instances, 50
+    RK4 steps, checkpoints every 10, shared 12x12 gain.  Loss, dL/dx0 and dL/dK
+    against the oracle's FP64 forward steps and reverse sweeps on the same
+    (for FP32: FP32-rounded) x0 and K; FP64 to 1e-11 of each row's scale, FP32
+    under the FP32 rule 2e-4 of each row's scale."""
+    N = 4096
+    x0, K = srb_inputs(N, seed=21)
+    tau = 1e-11 if dtype == "f64" else 2e-4
+    if dtype == "f32":
+        x0 = x0.astype(np.float32).astype(np.float64)
+        K = K.astype(np.float32).astype(np.float64)
+    prog = StepProgram(Function(programs.srb_step(), dtype=dtype), 144, 12)
+    L, _, gx, gK = _grad(prog, x0, K, 10)
+    orc = Oracle(programs.srb_step().to_bytes())
+    X = np.vstack([np.tile(K.reshape(144, 1), (1, N)), x0, np.zeros((1, N))])
+    for _ in range(STEPS):
+        X[144:] = orc.eval(X)
+    assert abs(L - X[156].sum()) <= tau * abs(X[156].sum())
+    rgx, rgK = _oracle_rollout_gradient(x0, K, STEPS)
+    assert np.all(np.abs(gx - rgx) <= tau * np.max(np.abs(rgx), axis=1, keepdims=True))
+    assert np.max(np.abs(gK - rgK)) <= tau * np.max(np.abs(rgK))
+
+
 def test_checkpointing_does_not_change_the_gradient(prog64):
     x0, K = srb_inputs(512, seed=6)
     L1, _, gx1, gK1 = _grad(prog64, x0, K, 10)

@@ -224,6 +224,30 @@ def test_eval_host_argument_errors_are_caught_on_the_host():
         L.cusadi_free(fn)
 
 
+def test_interpreter_work_slots_split_between_shared_memory_and_workspace():
+    """The interpreter keeps at most interp_shared_kb of work slots per
+    128-thread CTA in shared memory and the rest in workspace rows
+    ([rows x round_up(N, 128)]): no shared budget puts every slot in the
+    workspace, a larger budget never needs more rows."""
+    ir = programs.ldlt_spd_solve(22).to_bytes()
+    rows = []
+    for kb in (0, 16, 48, 200):
+        fn = L.cusadi_load(ir, _opt(path=L.CUSADI_PATH_INTERP, interp_shared_kb=kb))
+        try:
+            n_slots = L.cusadi_info(fn).n_slots
+            nb = L.cusadi_workspace_bytes(fn, 1000, False)
+            assert nb % (8 * 1024) == 0
+            rows.append(nb // (8 * 1024))
+            if kb == 0:
+                assert rows[-1] == n_slots
+        finally:
+            L.cusadi_free(fn)
+    assert rows == sorted(rows, reverse=True) and rows[-1] < rows[0]
+    assert rows[1] <= rows[0] - 16 * 1024 // (128 * 8)      # 16 KB = 16 shared slots of doubles
+    with pytest.raises(L.CusadiError):
+        L.cusadi_load(ir, _opt(path=L.CUSADI_PATH_INTERP, interp_shared_kb=201))
+
+
 def test_segmented_program_needs_a_workspace():
     ir = programs.random_program(3000, n_in=16, n_out=8, seed=5).to_bytes()
     fn = L.cusadi_load(ir, _opt(segment_ops=700, dtype=L.CUSADI_F32))

@@ -59,7 +59,7 @@ def test_noalloc_rejects_batches_beyond_the_scratch_size():
 def test_noalloc_interpreter_with_work_slots_in_the_scratch():
     from paper_2408_09662_gb300.experiments import _spd
     fn = Function(programs.ldlt_spd_solve(47), dtype="f64", path="interp")
-    assert not fn.compiled and fn.info.n_slots * 128 * 8 > 96 * 1024   # more slots than shared memory holds
+    assert not fn.compiled and fn.info.n_slots > 1000   # far more slots than shared memory holds
     N = 4099
     assert 0 < L.cusadi_workspace_bytes(fn.handle, N, False) <= L.CUSADI_NOALLOC_SCRATCH_BYTES
     x = torch.tensor(_spd(47, N, seed=47), device="cuda")
