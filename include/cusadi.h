@@ -117,6 +117,14 @@ typedef struct {
                                  last, live in the workspace; more shared memory
                                  means fewer resident CTAs, which costs more than the
                                  slots gain beyond ~48 KB on GB300                 (48) */
+  int32_t spill_values;       /* one-thread-per-instance kernels (ways = 0, inst_per_thread
+                                 = 1): > 0 keeps at most this many values live in
+                                 registers; linear scan over their live ranges moves the
+                                 value read last out of the registers for its whole life,
+                                 to a shared-memory slot, a workspace row beyond those,
+                                 or (inputs, carried values) a re-read of its buffer at
+                                 each use.  0: the compiler allocates registers    (0) */
+  int32_t spill_shared_kb;    /* shared memory per CTA for those values, KB (0..200) (96) */
   const char* cache_dir;      /* directory for compiled kernels, NULL = in-memory only */
 } cusadi_options;
 

@@ -334,6 +334,81 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
 
   const char* tin = G.buf_f64() ? "double" : "float";
   const char* tw = G.ws_f64() ? "double" : "float";
+  // Register budget (spill_values > 0, one instance per thread): per segment, a
+  // linear scan over the values' live ranges in statement order keeps at most
+  // spill_values of them in registers; when a value finds the budget full,
+  // whichever of it and the live register values is read last leaves the
+  // registers for its whole life (M. Poletto and V. Sarkar, "Linear scan
+  // register allocation", TOPLAS 1999).  An input or a value carried from an
+  // earlier kernel is then re-read from its buffer at each use; a computed value
+  // is stored once to a shared-memory slot (spill_shared_kb per CTA), or beyond
+  // those to a workspace row, and re-read at each use.  Accesses go through
+  // volatile pointers so that the compiler does not keep the value in a register.
+  enum { SP_REG = 0, SP_SMEM = 1, SP_WS = 2, SP_RELOAD = 3 };
+  std::vector<uint8_t> sp_kind(n, SP_REG);
+  std::vector<int64_t> sp_idx(n, -1);
+  int64_t sp_smem_slots = 0, sp_ws_rows = 0;
+  const bool spill = o.spill_values > 0 && !o.device_fn && std::max(1, o.inst_per_thread) == 1;
+  if (spill) {
+    const int64_t cap_sm = (int64_t)o.spill_shared_kb * 1024 / ((int64_t)o.block * (G.ws_f64() ? 8 : 4));
+    for (int s = 0; s < nseg; ++s) {
+      // positions: materialised operands of op i at 2i, its result at 2i + 1
+      std::vector<int64_t> def(n, -1), end(n, -1), order;
+      for (int64_t i = segs[s].first; i < segs[s].second; ++i) {
+        if (G.leaf(i)) continue;
+        const Node& x = g.nodes[i];
+        for (int32_t a : {x.a, x.b}) {
+          if (a < 0 || g.nodes[a].op == CONST) continue;
+          const bool outside = g.nodes[a].op == INPUT || G.seg_of[a] != s;
+          if (outside && def[a] < 0) { def[a] = 2 * i; order.push_back(a); }
+          end[a] = std::max(end[a], 2 * i + 1);
+        }
+        def[i] = 2 * i + 1;
+        end[i] = std::max(end[i], def[i]);
+        order.push_back(i);
+      }
+      std::set<std::pair<int64_t, int64_t>> active;   // (end, value) in registers
+      std::vector<int64_t> spilled;
+      for (int64_t v : order) {
+        while (!active.empty() && active.begin()->first <= def[v]) active.erase(active.begin());
+        if ((int64_t)active.size() < o.spill_values) { active.insert({end[v], v}); continue; }
+        auto last = std::prev(active.end());
+        if (last->first > end[v]) {
+          spilled.push_back(last->second);
+          active.erase(last);
+          active.insert({end[v], v});
+        } else {
+          spilled.push_back(v);
+        }
+      }
+      // memory slots of the spilled computed values: shared first, then workspace rows
+      std::sort(spilled.begin(), spilled.end(), [&](int64_t a, int64_t c) { return def[a] < def[c]; });
+      std::set<std::pair<int64_t, int64_t>> live_sm, live_ws;   // (end, slot)
+      std::vector<int64_t> free_sm, free_ws;
+      int64_t next_sm = 0, next_ws = 0;
+      for (int64_t v : spilled) {
+        if (def[v] == 2 * (def[v] / 2)) { sp_kind[v] = SP_RELOAD; continue; }   // input / carried value
+        while (!live_sm.empty() && live_sm.begin()->first <= def[v]) { free_sm.push_back(live_sm.begin()->second); live_sm.erase(live_sm.begin()); }
+        while (!live_ws.empty() && live_ws.begin()->first <= def[v]) { free_ws.push_back(live_ws.begin()->second); live_ws.erase(live_ws.begin()); }
+        if (!free_sm.empty() || next_sm < cap_sm) {
+          int64_t k;
+          if (!free_sm.empty()) { k = free_sm.back(); free_sm.pop_back(); } else k = next_sm++;
+          sp_kind[v] = SP_SMEM; sp_idx[v] = k; live_sm.insert({end[v], k});
+        } else {
+          int64_t k;
+          if (!free_ws.empty()) { k = free_ws.back(); free_ws.pop_back(); } else k = next_ws++;
+          sp_kind[v] = SP_WS; sp_idx[v] = k; live_ws.insert({end[v], k});
+        }
+      }
+      sp_smem_slots = std::max(sp_smem_slots, next_sm);
+      sp_ws_rows = std::max(sp_ws_rows, next_ws);
+    }
+    // spill rows follow the carried rows; every segment's run uses them afresh
+    for (int64_t v = 0; v < n; ++v)
+      if (sp_kind[v] == SP_WS) sp_idx[v] += R.ws_rows;
+    R.ws_rows += sp_ws_rows;
+    R.smem_bytes = sp_smem_slots * o.block * (G.ws_f64() ? 8 : 4);
+  }
   // Lanes: a kernel thread evaluates NL consecutive instances i .. i + NL - 1,
   // op by op in turn; their inputs and outputs move as one vector access when
   // the buffers allow it.  A kernel thread past the end of the batch still runs
@@ -361,6 +436,22 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
       const Node& x = g.nodes[i];
       bool f = G.node_f64(i);
       if (x.op == CONST) return lit(x.k, want_f64);
+      if (spill && sp_kind[i] != SP_REG) {
+        // read at each use from where the value lives
+        const char* W2 = G.ty(want_f64);
+        if (sp_kind[i] == SP_SMEM)
+          return std::string("((") + W2 + ")cs_sp[" + std::to_string(sp_idx[i]) + " * blockDim.x])";
+        if (sp_kind[i] == SP_WS)
+          return std::string("((") + W2 + ")Wv[" + std::to_string(sp_idx[i]) + "ll * ldw])";
+        if (x.op == INPUT) {
+          const bool second = o.split >= 0 && x.io >= o.split;
+          const int64_t row = second ? x.io - o.split : x.io;
+          const std::string base = second ? (x.bcast ? "X2b" : "X2") : (x.bcast ? "Xb" : "X");
+          return std::string("((") + W2 + ")((const volatile " + tin + "*)" + base + ")[" + std::to_string(row) +
+                 (second ? "ll * ldx2])" : "ll * ldx])");
+        }
+        return std::string("((") + W2 + ")Wv[" + std::to_string(G.ws_slot[i]) + "ll * ldw])";
+      }
       if (x.op == INPUT) {
         if (!have[i]) {
           have[i] = 1;
@@ -454,6 +545,10 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
         std::string B = x.b >= 0 ? operand(x.b, f, l) : "";
         body << "  const " << T << " " << vname(i, l) << " = " << op_expr(G, x, f, A, B, o) << ";\n";
       }
+      if (spill && sp_kind[i] == SP_SMEM)
+        body << "  cs_sp[" << sp_idx[i] << " * blockDim.x] = (" << tw << ")v" << i << ";\n";
+      else if (spill && sp_kind[i] == SP_WS)
+        body << "  Wv[" << sp_idx[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
       if (G.ws_slot[i] >= 0) {
         if (NL == 1) {
           body << "  if (active) W[" << G.ws_slot[i] << "ll * ldw] = (" << tw << ")v" << i << ";\n";
@@ -540,6 +635,12 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     src << "  const " << tin << "* __restrict__ Xb = X;\n"
         << "  const " << tin << "* __restrict__ X2b = X2;\n"
         << "  " << tin << "* __restrict__ Yb = Y;\n";
+    if (spill)   // values kept out of registers: shared slots and workspace rows, never cached
+      src << "  extern __shared__ __align__(16) unsigned char cs_smem[];\n"
+          << "  volatile " << tw << "* const cs_sp = reinterpret_cast<volatile " << tw
+          << "*>(cs_smem) + threadIdx.x;\n"
+          << "  volatile " << tw << "* const Wv = W + i;\n"
+          << "  (void)cs_sp; (void)Wv;\n";
     if (o.adjoint && R.has_reduce)
       src << "  " << tw << "* __restrict__ Wp = W + " << R.ws_rows << "ll * ldw + i;  // reduced-row terms\n";
     src << "  X += i; X2 += i; Y += i; W += i;\n"

@@ -115,6 +115,9 @@ struct CodegenOptions {
   int inst_per_thread = 1;       // one-thread kernels: R consecutive instances per thread
   int sync_every = 0;            // one-thread kernels: a CTA barrier every this many ops
   int coop_groups = 1;           // cooperative kernels: groups of 32 instances per CTA
+  int spill_values = 0;          // one-thread kernels: > 0 keeps at most this many values
+                                 // live in registers, the rest in shared memory / workspace
+  int spill_shared_kb = 96;      // shared memory per CTA for those values
   bool adjoint = false;
   int64_t split = -1;            // input rows >= split come from the second buffer
   bool device_fn = false;        // emit relocatable __device__ functions of one instance

@@ -223,6 +223,8 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.inst_per_thread = fn->opt.ways > 1 ? 1 : fn->opt.inst_per_thread;
   co.sync_every = fn->opt.ways > 1 ? 0 : fn->opt.sync_every;
   co.coop_groups = fn->opt.coop_groups;
+  co.spill_values = fn->opt.ways > 1 ? 0 : fn->opt.spill_values;
+  co.spill_shared_kb = fn->opt.spill_shared_kb;
   co.adjoint = adjoint;
   co.split = adjoint ? fn->ir.nnz_in : -1;
   static const char* tag[] = {"f64", "f32", "mixed"};
@@ -425,7 +427,7 @@ cusadi_status run(cusadi_fn fn, Direction& d, DevState& ds, bool adjoint, const 
   if (fn->opt.sync_every <= 0)
     while (block > 32 && ds.sms > 0 && (threads + block - 1) / block < ds.sms) block = (block / 2 + 31) / 32 * 32;
   unsigned grid = (unsigned)((threads + block - 1) / block);
-  unsigned smem = 0;
+  unsigned smem = (unsigned)d.cg.smem_bytes;   // register-budget spill slots (sized for opt.block)
   if (d.cg.coop_ways > 0) {   // W warps per group of 32 instances, G groups per CTA
     const int G = std::max(1, d.cg.coop_groups);
     block = 32u * (unsigned)d.cg.coop_ways * (unsigned)G;
@@ -524,6 +526,8 @@ void cusadi_default_options(cusadi_options* o) {
   o->coop_groups = 1;
   o->sync_every = 0;
   o->interp_shared_kb = 48;
+  o->spill_values = 0;
+  o->spill_shared_kb = 96;
   o->cache_dir = nullptr;
 }
 
@@ -576,6 +580,9 @@ cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* o
   if (o.sync_every < 0) return fail(CUSADI_E_INVALID_ARG, "sync_every must be >= 0");
   if (o.interp_shared_kb < 0 || o.interp_shared_kb > 200)
     return fail(CUSADI_E_INVALID_ARG, "interp_shared_kb must be in [0, 200]");
+  if (o.spill_values < 0) return fail(CUSADI_E_INVALID_ARG, "spill_values must be >= 0");
+  if (o.spill_shared_kb < 0 || o.spill_shared_kb > 200)
+    return fail(CUSADI_E_INVALID_ARG, "spill_shared_kb must be in [0, 200]");
   if (o.cache_dir) fn->cache_dir = o.cache_dir;
   o.cache_dir = nullptr;  // the caller's string is not kept
   auto t0 = std::chrono::steady_clock::now();

@@ -9,6 +9,7 @@ markdown table.
     python -m paper_2408_09662_gb300.experiments interp # interpreter vs compiled (LDL^T family)
     python -m paper_2408_09662_gb300.experiments one random20k f64 4096 8   # one kernel, for a profiler
     python -m paper_2408_09662_gb300.experiments one srb f64 65536 0 adjoint
+    python -m paper_2408_09662_gb300.experiments one fmachain f32 1245184 0   # the FMA-chain peak kernel
 
 ldlt: LDL^T solves of SPD systems, each about ten times the operations of the
 previous one, timed on the same inputs by the engine (compiled, or the
@@ -317,10 +318,13 @@ def interp_sweep(sizes=(22, 47), N=65536, budgets_kb=(0, 16, 48, 96)):
 def one_kernel(program="random20k", dtype="f64", N=4096, ways=0, reps=3, adjoint=False):
     """Compile one program and launch it `reps` times (a small case for a
     profiler); adjoint: its reverse sweep (broadcast rows reduced) instead."""
+    from . import peaks
     irs = {"random20k": lambda: programs.random_program(20000, seed=0),
            "cartpole": programs.cartpole_rk4, "mpc": programs.quadrotor_mpc,
-           "lqr": programs.quadrotor_lqr_step, "srb": programs.srb_step}
-    fn = Function(irs[program]().to_bytes(), dtype=dtype, ways=ways, adjoint=int(adjoint))
+           "lqr": programs.quadrotor_lqr_step, "srb": programs.srb_step,
+           "fmachain": lambda: peaks._chain_program("fma")}
+    extra = dict(schedule=0, inline_math=1) if program == "fmachain" else {}   # as peaks.py builds it
+    fn = Function(irs[program]().to_bytes(), dtype=dtype, ways=ways, adjoint=int(adjoint), **extra)
     x = torch.tensor(inputs.normal(fn.nnz_in, N, seed=1) * 0.1, dtype=fn.torch_dtype, device="cuda")
     y = fn(x)
     if adjoint:

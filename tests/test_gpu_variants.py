@@ -152,3 +152,39 @@ def test_own_math_out_of_line_equals_inlined(rand3k):
     orc = Oracle(rand3k)
     y = orc.eval(x)
     assert np.all(np.abs(got - y) <= tolerance(orc, x, y, 2e-4, kind=1))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "mixed"])
+def test_register_budget_spills_give_the_same_bits(rand3k, dtype):
+    """spill_values caps the values a thread keeps in registers; the rest live
+    in shared-memory slots, in workspace rows (a 4 KB shared budget forces
+    those) or are re-read from their input / carried row.  Only where values
+    live changes, so the results keep their bits."""
+    ir = rand3k if dtype != "mixed" else programs.quadrotor_mpc(dict(programs.QUADROTOR, M=1)).to_bytes()
+    x = (inputs.normal(64, 4099, seed=27) if dtype != "mixed" else
+         np.vstack([np.random.default_rng(3).uniform(-0.5, 0.5, (6, 4099)),
+                    np.random.default_rng(4).uniform(-1, 1, (2, 4099))]))
+    x = x.astype(np.float32).astype(np.float64)
+    ref, _ = _eval(Function(ir, dtype=dtype, fmad=0), x)
+    for opts in (dict(spill_values=24), dict(spill_values=24, spill_shared_kb=4, segment_ops=900)):
+        fn = Function(ir, dtype=dtype, fmad=0, **opts)
+        got, buf = _eval(fn, x, ld=4099 + 5)
+        np.testing.assert_array_equal(got, ref, err_msg=str(opts))
+        assert torch.all(buf[:, 4099:] == 7.0)
+
+
+def test_register_budget_in_the_adjoint():
+    ir = programs.srb_step().to_bytes()
+    rng = np.random.default_rng(29)
+    N = 2051
+    X = np.vstack([np.tile(rng.normal(0, 0.1, (144, 1)), (1, N)), rng.uniform(-0.1, 0.1, (12, N)),
+                   np.zeros((1, N))])
+    ybar = rng.standard_normal((13, N))
+    res = []
+    for opts in ({}, dict(spill_values=32, spill_shared_kb=8)):
+        fn = Function(ir, dtype="f64", fmad=0, **opts)
+        a = fn.adjoint(torch.tensor(X, device="cuda"), torch.tensor(ybar, device="cuda"), reduce_broadcast=True)
+        torch.cuda.synchronize()
+        res.append((a[:144, 0].cpu().numpy(), a[144:].cpu().numpy()))
+    for u, v in zip(*res):
+        np.testing.assert_array_equal(u, v)
