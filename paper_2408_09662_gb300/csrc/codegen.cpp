@@ -345,69 +345,75 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
   // those to a workspace row, and re-read at each use.  Accesses go through
   // volatile pointers so that the compiler does not keep the value in a register.
   enum { SP_REG = 0, SP_SMEM = 1, SP_WS = 2, SP_RELOAD = 3 };
+  // where each value lives in the segment being generated (a value carried into
+  // a later segment is placed afresh there)
   std::vector<uint8_t> sp_kind(n, SP_REG);
   std::vector<int64_t> sp_idx(n, -1);
-  int64_t sp_smem_slots = 0, sp_ws_rows = 0;
   const bool spill = o.spill_values > 0 && !o.device_fn && std::max(1, o.inst_per_thread) == 1;
-  if (spill) {
-    const int64_t cap_sm = (int64_t)o.spill_shared_kb * 1024 / ((int64_t)o.block * (G.ws_f64() ? 8 : 4));
-    for (int s = 0; s < nseg; ++s) {
-      // positions: materialised operands of op i at 2i, its result at 2i + 1
-      std::vector<int64_t> def(n, -1), end(n, -1), order;
-      for (int64_t i = segs[s].first; i < segs[s].second; ++i) {
-        if (G.leaf(i)) continue;
-        const Node& x = g.nodes[i];
-        for (int32_t a : {x.a, x.b}) {
-          if (a < 0 || g.nodes[a].op == CONST) continue;
-          const bool outside = g.nodes[a].op == INPUT || G.seg_of[a] != s;
-          if (outside && def[a] < 0) { def[a] = 2 * i; order.push_back(a); }
-          end[a] = std::max(end[a], 2 * i + 1);
-        }
-        def[i] = 2 * i + 1;
-        end[i] = std::max(end[i], def[i]);
-        order.push_back(i);
+  const int64_t sp_cap_sm = (int64_t)o.spill_shared_kb * 1024 / ((int64_t)o.block * (G.ws_f64() ? 8 : 4));
+  const int64_t sp_ws_base = R.ws_rows;   // spill rows follow the carried rows
+  // fills sp_kind / sp_idx for segment s; returns (shared slots, workspace rows) used
+  auto spill_segment = [&](int s) -> std::pair<int64_t, int64_t> {
+    std::fill(sp_kind.begin(), sp_kind.end(), (uint8_t)SP_REG);
+    std::fill(sp_idx.begin(), sp_idx.end(), (int64_t)-1);
+    // positions: materialised operands of op i at 2i, its result at 2i + 1
+    std::vector<int64_t> def(n, -1), end(n, -1), order;
+    for (int64_t i = segs[s].first; i < segs[s].second; ++i) {
+      if (G.leaf(i)) continue;
+      const Node& x = g.nodes[i];
+      for (int32_t a : {x.a, x.b}) {
+        if (a < 0 || g.nodes[a].op == CONST) continue;
+        const bool outside = g.nodes[a].op == INPUT || G.seg_of[a] != s;
+        if (outside && def[a] < 0) { def[a] = 2 * i; order.push_back(a); }
+        end[a] = std::max(end[a], 2 * i + 1);
       }
-      std::set<std::pair<int64_t, int64_t>> active;   // (end, value) in registers
-      std::vector<int64_t> spilled;
-      for (int64_t v : order) {
-        while (!active.empty() && active.begin()->first <= def[v]) active.erase(active.begin());
-        if ((int64_t)active.size() < o.spill_values) { active.insert({end[v], v}); continue; }
-        auto last = std::prev(active.end());
-        if (last->first > end[v]) {
-          spilled.push_back(last->second);
-          active.erase(last);
-          active.insert({end[v], v});
-        } else {
-          spilled.push_back(v);
-        }
-      }
-      // memory slots of the spilled computed values: shared first, then workspace rows
-      std::sort(spilled.begin(), spilled.end(), [&](int64_t a, int64_t c) { return def[a] < def[c]; });
-      std::set<std::pair<int64_t, int64_t>> live_sm, live_ws;   // (end, slot)
-      std::vector<int64_t> free_sm, free_ws;
-      int64_t next_sm = 0, next_ws = 0;
-      for (int64_t v : spilled) {
-        if (def[v] == 2 * (def[v] / 2)) { sp_kind[v] = SP_RELOAD; continue; }   // input / carried value
-        while (!live_sm.empty() && live_sm.begin()->first <= def[v]) { free_sm.push_back(live_sm.begin()->second); live_sm.erase(live_sm.begin()); }
-        while (!live_ws.empty() && live_ws.begin()->first <= def[v]) { free_ws.push_back(live_ws.begin()->second); live_ws.erase(live_ws.begin()); }
-        if (!free_sm.empty() || next_sm < cap_sm) {
-          int64_t k;
-          if (!free_sm.empty()) { k = free_sm.back(); free_sm.pop_back(); } else k = next_sm++;
-          sp_kind[v] = SP_SMEM; sp_idx[v] = k; live_sm.insert({end[v], k});
-        } else {
-          int64_t k;
-          if (!free_ws.empty()) { k = free_ws.back(); free_ws.pop_back(); } else k = next_ws++;
-          sp_kind[v] = SP_WS; sp_idx[v] = k; live_ws.insert({end[v], k});
-        }
-      }
-      sp_smem_slots = std::max(sp_smem_slots, next_sm);
-      sp_ws_rows = std::max(sp_ws_rows, next_ws);
+      def[i] = 2 * i + 1;
+      end[i] = std::max(end[i], def[i]);
+      order.push_back(i);
     }
-    // spill rows follow the carried rows; every segment's run uses them afresh
-    for (int64_t v = 0; v < n; ++v)
-      if (sp_kind[v] == SP_WS) sp_idx[v] += R.ws_rows;
-    R.ws_rows += sp_ws_rows;
-    R.smem_bytes = sp_smem_slots * o.block * (G.ws_f64() ? 8 : 4);
+    std::set<std::pair<int64_t, int64_t>> active;   // (end, value) in registers
+    std::vector<int64_t> spilled;
+    for (int64_t v : order) {
+      while (!active.empty() && active.begin()->first <= def[v]) active.erase(active.begin());
+      if ((int64_t)active.size() < o.spill_values) { active.insert({end[v], v}); continue; }
+      auto last = std::prev(active.end());
+      if (last->first > end[v]) {
+        spilled.push_back(last->second);
+        active.erase(last);
+        active.insert({end[v], v});
+      } else {
+        spilled.push_back(v);
+      }
+    }
+    // memory slots of the spilled computed values: shared first, then workspace rows
+    std::sort(spilled.begin(), spilled.end(), [&](int64_t a, int64_t c) { return def[a] < def[c]; });
+    std::set<std::pair<int64_t, int64_t>> live_sm, live_ws;   // (end, slot)
+    std::vector<int64_t> free_sm, free_ws;
+    int64_t next_sm = 0, next_ws = 0;
+    for (int64_t v : spilled) {
+      if (def[v] % 2 == 0) { sp_kind[v] = SP_RELOAD; continue; }   // input / carried value
+      while (!live_sm.empty() && live_sm.begin()->first <= def[v]) { free_sm.push_back(live_sm.begin()->second); live_sm.erase(live_sm.begin()); }
+      while (!live_ws.empty() && live_ws.begin()->first <= def[v]) { free_ws.push_back(live_ws.begin()->second); live_ws.erase(live_ws.begin()); }
+      int64_t k;
+      if (!free_sm.empty() || next_sm < sp_cap_sm) {
+        if (!free_sm.empty()) { k = free_sm.back(); free_sm.pop_back(); } else k = next_sm++;
+        sp_kind[v] = SP_SMEM; sp_idx[v] = k; live_sm.insert({end[v], k});
+      } else {
+        if (!free_ws.empty()) { k = free_ws.back(); free_ws.pop_back(); } else k = next_ws++;
+        sp_kind[v] = SP_WS; sp_idx[v] = sp_ws_base + k; live_ws.insert({end[v], k});
+      }
+    }
+    return {next_sm, next_ws};
+  };
+  if (spill) {   // sizes: the most any segment needs (the segments run one after the other)
+    int64_t sm = 0, ws = 0;
+    for (int s = 0; s < nseg; ++s) {
+      auto u = spill_segment(s);
+      sm = std::max(sm, u.first);
+      ws = std::max(ws, u.second);
+    }
+    R.ws_rows += ws;
+    R.smem_bytes = sm * o.block * (G.ws_f64() ? 8 : 4);
   }
   // Lanes: a kernel thread evaluates NL consecutive instances i .. i + NL - 1,
   // op by op in turn; their inputs and outputs move as one vector access when
@@ -427,6 +433,7 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
   };
 
   for (int s = 0; s < nseg; ++s) {
+    if (spill) spill_segment(s);
     std::ostringstream body;
     std::vector<uint8_t> have(n, 0);   // leaf or ws value materialised in this segment
     std::vector<uint8_t> decl_buf(n, 0);  // lanes declared with the buffer's type, not the op's

@@ -248,6 +248,47 @@ def test_interpreter_work_slots_split_between_shared_memory_and_workspace():
         L.cusadi_load(ir, _opt(path=L.CUSADI_PATH_INTERP, interp_shared_kb=201))
 
 
+@pytest.mark.parametrize("prog,opts", [
+    ("random3k", dict(dtype=L.CUSADI_F64, spill_values=24, spill_shared_kb=4, segment_ops=900)),
+    ("random3k", dict(dtype=L.CUSADI_F32, spill_values=16, segment_ops=700)),
+    ("mpc", dict(dtype=L.CUSADI_MIXED, spill_values=96))])
+def test_register_budget_reads_follow_writes_in_every_kernel(prog, opts):
+    """Under a register budget a value out of registers is stored once to its
+    shared slot (cs_sp) or spill row (Wv) and re-read at each use.  Every read
+    of a slot must come after a store to it in the same kernel, and every read
+    of a row after a store in the same kernel or a carried row stored by an
+    earlier kernel: the slots and spill rows of one kernel mean nothing in the
+    next."""
+    ir = {"random3k": lambda: programs.random_program(3000, seed=61),
+          "mpc": lambda: programs.quadrotor_mpc()}[prog]().to_bytes()
+    fn = L.cusadi_load(ir, _opt(**opts))
+    try:
+        carried, spilled_any = set(), False
+        for seg in range(L.cusadi_info(fn).n_segments):
+            src = L.cusadi_source(fn, False, seg)
+            body = src[src.index("__global__"):]
+            slots, rows = set(), set()
+            for line in body.splitlines():
+                st = line.strip()
+                for m in re.finditer(r"cs_sp\[(\d+) \* blockDim\.x\]", line):
+                    k = int(m.group(1))
+                    if st.startswith(f"cs_sp[{k} "):
+                        slots.add(k)
+                    else:
+                        assert k in slots, (seg, line)
+                for m in re.finditer(r"Wv\[(\d+)ll \* ldw\]", line):
+                    r = int(m.group(1))
+                    if st.startswith(f"Wv[{r}ll"):
+                        rows.add(r)
+                    else:
+                        assert r in rows or r in carried, (seg, line)
+            spilled_any |= bool(slots or rows)
+            carried |= {int(r) for r in re.findall(r"\bW\[(\d+)ll \* ldw\] =", body)}
+        assert spilled_any
+    finally:
+        L.cusadi_free(fn)
+
+
 def test_segmented_program_needs_a_workspace():
     ir = programs.random_program(3000, n_in=16, n_out=8, seed=5).to_bytes()
     fn = L.cusadi_load(ir, _opt(segment_ops=700, dtype=L.CUSADI_F32))
