@@ -42,7 +42,7 @@ NOMINAL_FMA_PER_S = {"f64": 1.25e12 / 2, "f32": 152 * 128 * 2.07e9}
 # DRAM bytes (read + write) per launch that an ncu capture measured for the
 # generated kernel with this source hash; a kernel whose source changed since
 # the capture gets no traffic figure (null) rather than a stale one
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"7f243409b56b79cf": 26300672 + 10496}   # 4 warps per 32 instances, 2 groups per CTA
 
 
 def workload_config(info=None):
@@ -449,6 +449,8 @@ def run_experiment(name):
         experiments.batch_sweep()
     elif name == "interp":
         experiments.interp_sweep()
+    elif name == "spill":
+        experiments.spill_sweep()
     else:
         from oracle import Oracle
         cores = os.cpu_count() or 1
@@ -487,7 +489,7 @@ def main():
                          '"coop_groups": 2}\'): no tuning')
     ap.add_argument("--launch32", default=None,
                     help="fixed launch options of the FP32 kernel as JSON: no tuning")
-    ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc", "roa", "batch", "interp"],
+    ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc", "roa", "batch", "interp", "spill"],
                     help="run one of the paper's experiments instead (markdown table, no JSON line); "
                          "ldlt adds the CPU oracle as its CPU baseline column")
     args = ap.parse_args()

@@ -7,6 +7,7 @@ markdown table.
     python -m paper_2408_09662_gb300.experiments mpc    # MPC cost/violation vs iterations (§V-A, Fig. 4)
     python -m paper_2408_09662_gb300.experiments batch  # uneven batch: satellite widths
     python -m paper_2408_09662_gb300.experiments interp # interpreter vs compiled (LDL^T family)
+    python -m paper_2408_09662_gb300.experiments spill  # register budget on the MPC and LQR steps
     python -m paper_2408_09662_gb300.experiments one random20k f64 4096 8   # one kernel, for a profiler
     python -m paper_2408_09662_gb300.experiments one srb f64 65536 0 adjoint
     python -m paper_2408_09662_gb300.experiments one fmachain f32 1245184 0   # the FMA-chain peak kernel
@@ -315,6 +316,35 @@ def interp_sweep(sizes=(22, 47), N=65536, budgets_kb=(0, 16, 48, 96)):
     return rows
 
 
+def spill_sweep(reps=7):
+    """The register budget (spill_values) on the programs with the most live
+    values: the closed-form MPC (906 at once) at N = 16,384 and the LQR step
+    (255) at N = 10,000, against the compiler's own register allocation."""
+    rng = np.random.default_rng(2)
+    mpc_x = np.vstack([rng.uniform(-0.5, 0.5, (6, 16384)), rng.uniform(-1, 1, (2, 16384))])
+    r = np.random.default_rng(0)
+    N = 10000
+    lqr_x = np.vstack([r.uniform(-0.5, 0.5, (6, N)), r.uniform(10, 20, (1, N)), r.uniform(0.8, 1.2, (1, N)),
+                       r.uniform(0.008, 0.012, (1, N)), r.uniform(0.5, 10, (6, N)), r.uniform(0.05, 0.5, (1, N))])
+    work = [("quadrotor MPC", programs.quadrotor_mpc().to_bytes(), dt, mpc_x, sv)
+            for dt in ("f64", "mixed") for sv in (0, 112, 96, 64)]
+    work += [("LQR step", programs.quadrotor_lqr_step().to_bytes(), "f64", lqr_x, sv) for sv in (0, 112, 80)]
+    with ThreadPoolExecutor(8) as ex:
+        fns = list(ex.map(lambda w: Function(w[1], dtype=w[2], spill_values=w[4]), work))
+    print("| program | dtype | N | register budget (values) | ms | max abs diff vs no budget |")
+    print("|---|---|---|---|---|---|")
+    ref, rows = {}, []
+    for (name, _, dt, X, sv), fn in zip(work, fns):
+        x = torch.tensor(X, dtype=fn.torch_dtype, device="cuda")
+        y = torch.empty((fn.nnz_out, X.shape[1]), dtype=fn.torch_dtype, device="cuda")
+        ms = _gpu_ms(lambda: fn(x, out=y), reps=reps)
+        yn = y.double().cpu().numpy()
+        d = float(np.max(np.abs(yn - ref.setdefault((name, dt), yn))))
+        rows.append((name, dt, X.shape[1], sv, ms, d))
+        print(f"| {name} | {dt} | {X.shape[1]} | {sv or 'none'} | {ms:.3f} | {d:.1e} |", flush=True)
+    return rows
+
+
 def one_kernel(program="random20k", dtype="f64", N=4096, ways=0, reps=3, adjoint=False):
     """Compile one program and launch it `reps` times (a small case for a
     profiler); adjoint: its reverse sweep (broadcast rows reduced) instead."""
@@ -354,6 +384,8 @@ def main(argv):
         batch_sweep()
     elif which == "interp":
         interp_sweep()
+    elif which == "spill":
+        spill_sweep()
     elif which == "one":
         # one <program> <dtype> <N> <ways> [adjoint]
         prog, dt, N, w = (argv[2:] + ["random20k", "f64", "4096", "0"][len(argv) - 2:])[:4]
