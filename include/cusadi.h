@@ -125,6 +125,12 @@ typedef struct {
                                  or (inputs, carried values) a re-read of its buffer at
                                  each use.  0: the compiler allocates registers    (0) */
   int32_t spill_shared_kb;    /* shared memory per CTA for those values, KB (0..200) (96) */
+  int32_t pair_calls;         /* one-thread-per-instance kernels: > 0 issues an out-of-line
+                                 unary math call (sin, cos, exp, ...) together with a later
+                                 call of the same function, at most this many ops ahead,
+                                 whose argument is already computed: one call of a
+                                 two-argument version evaluating both.  0: one call per
+                                 op                                                 (0) */
   const char* cache_dir;      /* directory for compiled kernels, NULL = in-memory only */
 } cusadi_options;
 

@@ -40,7 +40,7 @@ class cusadi_options(ctypes.Structure):
                 ("inline_math", c_int32), ("adjoint", c_int32), ("ways", c_int32), ("own_math", c_int32),
                 ("debug_checks", c_int32), ("inst_per_thread", c_int32), ("coop_groups", c_int32),
                 ("sync_every", c_int32), ("interp_shared_kb", c_int32), ("spill_values", c_int32),
-                ("spill_shared_kb", c_int32),
+                ("spill_shared_kb", c_int32), ("pair_calls", c_int32),
                 ("cache_dir", c_char_p)]
 
 

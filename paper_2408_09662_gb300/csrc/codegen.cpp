@@ -83,6 +83,7 @@ struct Gen {
   std::vector<int64_t> ws_slot;     // workspace row of values crossing a cut
   std::vector<std::vector<int64_t>> out_rows;  // per node: output rows it feeds
   std::set<std::pair<int, bool>> calls;        // (op, f64) of out-of-line math used
+  std::set<std::pair<int, bool>> calls2;       // (op, f64) of the paired (two-argument) versions
   bool own_f32 = false;                        // own FP32 sin/cos/exp used
 
   Gen(const Graph& g_, const CodegenOptions& o_) : g(g_), o(o_) {}
@@ -432,12 +433,41 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
     return l;
   };
 
+  // Paired calls: an out-of-line unary math call (sin, cos, exp, ...) is issued
+  // together with a later call of the same function whose argument is already
+  // computed, as one call of a two-argument version: half the call overhead, and
+  // the two evaluations inside it are independent work the compiler can overlap.
+  const bool pairing = o.pair_calls > 0 && NL == 1 && !spill && o.inline_math != 1;
+  auto pairable = [&](int64_t i) {
+    const Node& x = g.nodes[i];
+    if (G.leaf(i) || !op_call(x.op) || op_arity(x.op) != 1 || inlined(x.op, o.inline_math)) return false;
+    return !( !G.node_f64((int32_t)i) && o.own_math && own_f32_math(x.op));
+  };
+  std::vector<int64_t> partner(n, -1);
+  std::vector<uint8_t> hoisted(n, 0);
   for (int s = 0; s < nseg; ++s) {
     if (spill) spill_segment(s);
+    if (pairing) {
+      for (int64_t i = segs[s].first; i < segs[s].second; ++i) {
+        if (!pairable(i) || hoisted[i]) continue;
+        const int64_t lim = std::min<int64_t>(segs[s].second, i + 1 + o.pair_calls);
+        for (int64_t j = i + 1; j < lim; ++j) {
+          if (!pairable(j) || hoisted[j] || partner[j] >= 0 || g.nodes[j].op != g.nodes[i].op ||
+              G.node_f64((int32_t)j) != G.node_f64((int32_t)i))
+            continue;
+          const int32_t a = g.nodes[j].a;   // available at i: a leaf, carried in, or computed before i
+          if (!(G.leaf(a) || G.seg_of[a] != s || a < i)) continue;
+          partner[i] = j;
+          hoisted[j] = 1;
+          break;
+        }
+      }
+    }
     std::ostringstream body;
     std::vector<uint8_t> have(n, 0);   // leaf or ws value materialised in this segment
     std::vector<uint8_t> decl_buf(n, 0);  // lanes declared with the buffer's type, not the op's
     G.calls.clear();
+    G.calls2.clear();
     G.own_f32 = false;
     auto operand = [&](int32_t i, bool want_f64, int r) -> std::string {
       const Node& x = g.nodes[i];
@@ -547,10 +577,21 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
       const Node& x = g.nodes[i];
       const bool f = G.node_f64((int32_t)i);
       const char* T = G.ty(f);
-      for (int l = 0; l < NL; ++l) {
-        std::string A = x.a >= 0 ? operand(x.a, f, l) : "";
-        std::string B = x.b >= 0 ? operand(x.b, f, l) : "";
-        body << "  const " << T << " " << vname(i, l) << " = " << op_expr(G, x, f, A, B, o) << ";\n";
+      if (pairing && partner[i] >= 0) {
+        const int64_t j = partner[i];
+        std::string A = operand(x.a, f, 0), Aj = operand(g.nodes[j].a, f, 0);
+        G.calls2.insert({x.op, f});
+        MathFn m = math_name(x.op);
+        body << "  const " << T << "2 p" << i << " = cs_" << m.d << "2" << (f ? "_d" : "_f") << "(" << A
+             << ", " << Aj << ");\n"
+             << "  const " << T << " v" << i << " = p" << i << ".x;\n"
+             << "  const " << T << " v" << j << " = p" << i << ".y;\n";
+      } else if (!(pairing && hoisted[i])) {    // a hoisted op was computed with its partner
+        for (int l = 0; l < NL; ++l) {
+          std::string A = x.a >= 0 ? operand(x.a, f, l) : "";
+          std::string B = x.b >= 0 ? operand(x.b, f, l) : "";
+          body << "  const " << T << " " << vname(i, l) << " = " << op_expr(G, x, f, A, B, o) << ";\n";
+        }
       }
       if (spill && sp_kind[i] == SP_SMEM)
         body << "  cs_sp[" << sp_idx[i] << " * blockDim.x] = (" << tw << ")v" << i << ";\n";
@@ -593,6 +634,14 @@ CodegenResult generate(const Graph& g, const CodegenOptions& o) {
         src << "static __device__ __noinline__ " << t << " " << call_name(c.first, c.second, false) << "("
             << t << " a" << (bin ? std::string(", ") + t + " b" : "") << ") { return "
             << (c.second ? m.d : m.f) << "(a" << (bin ? ", b" : "") << "); }\n";
+      }
+      for (auto& c : G.calls2) {   // two independent evaluations per call
+        MathFn m = math_name(c.first);
+        const char* t = c.second ? "double" : "float";
+        const char* fn = c.second ? m.d : m.f;
+        src << "static __device__ __noinline__ " << t << "2 cs_" << m.d << "2" << (c.second ? "_d" : "_f")
+            << "(" << t << " a, " << t << " b) { " << t << "2 r; r.x = " << fn << "(a); r.y = " << fn
+            << "(b); return r; }\n";
       }
     }
     std::string name = o.prefix + "_" + std::to_string(s);

@@ -118,6 +118,9 @@ struct CodegenOptions {
   int spill_values = 0;          // one-thread kernels: > 0 keeps at most this many values
                                  // live in registers, the rest in shared memory / workspace
   int spill_shared_kb = 96;      // shared memory per CTA for those values
+  int pair_calls = 0;            // one-thread kernels: > 0 evaluates two calls of the same
+                                 // out-of-line math function at once, the second hoisted
+                                 // from at most this many ops later
   bool adjoint = false;
   int64_t split = -1;            // input rows >= split come from the second buffer
   bool device_fn = false;        // emit relocatable __device__ functions of one instance

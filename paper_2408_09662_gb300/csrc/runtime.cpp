@@ -225,6 +225,7 @@ cusadi_status compile_direction(cusadi_fn fn, Direction& d, bool adjoint) {
   co.coop_groups = fn->opt.coop_groups;
   co.spill_values = fn->opt.ways > 1 ? 0 : fn->opt.spill_values;
   co.spill_shared_kb = fn->opt.spill_shared_kb;
+  co.pair_calls = fn->opt.ways > 1 ? 0 : fn->opt.pair_calls;
   co.adjoint = adjoint;
   co.split = adjoint ? fn->ir.nnz_in : -1;
   static const char* tag[] = {"f64", "f32", "mixed"};
@@ -528,6 +529,7 @@ void cusadi_default_options(cusadi_options* o) {
   o->interp_shared_kb = 48;
   o->spill_values = 0;
   o->spill_shared_kb = 96;
+  o->pair_calls = 0;
   o->cache_dir = nullptr;
 }
 
@@ -581,6 +583,7 @@ cusadi_status cusadi_load(const void* ir, size_t nbytes, const cusadi_options* o
   if (o.interp_shared_kb < 0 || o.interp_shared_kb > 200)
     return fail(CUSADI_E_INVALID_ARG, "interp_shared_kb must be in [0, 200]");
   if (o.spill_values < 0) return fail(CUSADI_E_INVALID_ARG, "spill_values must be >= 0");
+  if (o.pair_calls < 0) return fail(CUSADI_E_INVALID_ARG, "pair_calls must be >= 0");
   if (o.spill_shared_kb < 0 || o.spill_shared_kb > 200)
     return fail(CUSADI_E_INVALID_ARG, "spill_shared_kb must be in [0, 200]");
   if (o.cache_dir) fn->cache_dir = o.cache_dir;

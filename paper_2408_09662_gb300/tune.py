@@ -13,15 +13,17 @@ keyed by the program's content hash, the GPU, the dtype, the batch size (to
 the next power of two) and the caller's fixed options, so a later call loads
 the chosen kernel directly.
 
-Search, in two rounds:
+Search, in three rounds:
 1. shape: ways in `ways` (0 = one thread per instance, W = W warps per group
    of 32 instances);
 2. around the best shape of each family (ways = 0 and ways > 0): for ways = 0,
    instances per thread (2, 4) and register caps (128, 96, 64: measured on
    GB300, a cap of 128 takes the random 20k-op FP32 kernel from 0.61 to 0.37 ms
    and 64 the cart-pole FP64 kernel from 0.142 to 0.115 ms); for ways > 0, 2 or
-   4 groups of 32 instances per CTA.  (CTA barriers every few hundred ops,
-   sync_every, measured no faster on any program and are not searched.)
+   4 groups of 32 instances per CTA;
+3. a one-thread winner with paired out-of-line math calls (pair_calls).
+(CTA barriers every few hundred ops, sync_every, and the engine's register
+budget, spill_values, measured no faster on any program and are not searched.)
 """
 from __future__ import annotations
 
@@ -140,6 +142,11 @@ def autotune(program, x: torch.Tensor, dtype: str = "f64", ways=(0, 2, 4, 8), re
                 info = tried[best][1].info
                 cands += _refinements(dict(best), dtype, info.n_ops, info.n_slots)
         run_round(cands)
+        # a one-thread winner also tries paired math calls (sin/cos/exp issued two
+        # at a time; measured 4 % on the random 20k-op FP32 kernel)
+        best = min(tried, key=lambda k: tried[k][0])
+        if dict(best).get("ways", 0) == 0 and dict(best).get("inst_per_thread", 1) == 1:
+            run_round([dict(dict(best), pair_calls=256)])
     best = min(tried, key=lambda k: tried[k][0])
     ms, fn = tried[best]
     rec = {"options": dict(best), "ms": ms, "N": N,

@@ -188,3 +188,18 @@ def test_register_budget_in_the_adjoint():
         res.append((a[:144, 0].cpu().numpy(), a[144:].cpu().numpy()))
     for u, v in zip(*res):
         np.testing.assert_array_equal(u, v)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_paired_math_calls_give_the_same_bits(rand3k, dtype):
+    """pair_calls evaluates two calls of the same out-of-line function in one
+    call (the second hoisted from a few ops later): the same function on the
+    same argument, so the same bits."""
+    x = inputs.normal(64, 4099, seed=31).astype(np.float32).astype(np.float64)
+    ref, _ = _eval(Function(rand3k, dtype=dtype, fmad=0), x)
+    for window in (8, 256):
+        fn = Function(rand3k, dtype=dtype, fmad=0, pair_calls=window)
+        assert "2_" + ("d" if dtype == "f64" else "f") + "(" in fn.source()
+        got, buf = _eval(fn, x, ld=4099 + 1)
+        np.testing.assert_array_equal(got, ref, err_msg=f"window {window}")
+        assert torch.all(buf[:, 4099:] == 7.0)

@@ -289,6 +289,28 @@ def test_register_budget_reads_follow_writes_in_every_kernel(prog, opts):
         L.cusadi_free(fn)
 
 
+def test_paired_calls_compile_and_cover_both_ops():
+    """With pair_calls a sin/cos/exp call is issued with a later one of the same
+    function whose argument already exists; the generated kernel compiles (so
+    every argument is declared before its use) and each paired op's value is
+    defined exactly once."""
+    ir = programs.random_program(3000, seed=61).to_bytes()
+    fn = L.cusadi_load(ir, _opt(dtype=L.CUSADI_F32, pair_calls=64, segment_ops=1200))
+    try:
+        n_pairs = 0
+        for seg in range(L.cusadi_info(fn).n_segments):
+            src = L.cusadi_source(fn, False, seg)
+            pairs = re.findall(r"const float2 p(\d+) = cs_(sin|cos|exp)2_f\(", src)
+            n_pairs += len(pairs)
+            defs = re.findall(r"const float (v\d+) = ", src)
+            assert len(defs) == len(set(defs))
+        assert n_pairs > 0
+    finally:
+        L.cusadi_free(fn)
+    with pytest.raises(L.CusadiError):
+        L.cusadi_load(ir, _opt(pair_calls=-1))
+
+
 def test_segmented_program_needs_a_workspace():
     ir = programs.random_program(3000, n_in=16, n_out=8, seed=5).to_bytes()
     fn = L.cusadi_load(ir, _opt(segment_ops=700, dtype=L.CUSADI_F32))
