@@ -494,6 +494,7 @@ def main():
                          "ldlt adds the CPU oracle as its CPU baseline column")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    t_main = time.perf_counter()
     if args.experiment:
         run_experiment(args.experiment)
         return
@@ -537,8 +538,10 @@ def main():
             fn.tune_record = {"options": opts, "candidates": [], "fixed": True}
             return fn
         return autotune(ir, x, dt, ways=cand[dt], use_cache=False)
+    t_tune = time.perf_counter()
     fn64 = launch("f64", args.launch64, x64)      # one after the other:
     fn32 = launch("f32", args.launch32, x32)      # nothing else on the GPU
+    t_tune = time.perf_counter() - t_tune
     tuning = {dt: {"chosen": fn.tune_record["options"],
                    "candidates_ms": [[json.dumps(o, sort_keys=True), ms] for o, ms in fn.tune_record["candidates"]]}
               for dt, fn in (("f64", fn64), ("f32", fn32))}
@@ -662,7 +665,7 @@ def main():
                               "kernel), coop_groups such groups per CTA; ways = 0: one thread "
                               "per instance, inst_per_thread instances each, maxrregcount a "
                               "register cap"),
-        "launch_tuning_ms": tuning,
+        "launch_tuning_ms": tuning, "launch_tuning_seconds": t_tune,
         "gop_per_s": ops_live * N_INST / t64 * 1e-9,
         "roofline": {"bound": "alu", "achieved": ach64 * 1e-12,
                      "peak": NOMINAL_FMA_PER_S["f64"] * 1e-12,
@@ -710,6 +713,7 @@ def main():
     }
     if extra is not None:
         line["adjoint_forward_ratio"] = extra["srb_rollout"]["f64"]["adjoint_forward_ratio"]
+    line["bench_wall_seconds"] = time.perf_counter() - t_main
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

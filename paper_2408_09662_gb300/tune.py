@@ -99,7 +99,7 @@ def _time(fn: Function, x: torch.Tensor, y: torch.Tensor, flush: torch.Tensor, r
 
 def autotune(program, x: torch.Tensor, dtype: str = "f64", ways=(0, 2, 4, 8), refine: bool = True,
              reps: int = 5, flush_bytes: int = 256 << 20, cache_dir=DEFAULT_CACHE,
-             use_cache: bool = True, compile_workers: int = 4, **fixed) -> Function:
+             use_cache: bool = True, compile_workers: int = 8, **fixed) -> Function:
     """The program compiled in the fastest configuration found for the batch x
     ([nnz_in, N] CUDA tensor of the dtype's element type).  `fixed` options
     (e.g. fmad=0) apply to every candidate.  The returned Function carries
