@@ -171,17 +171,24 @@ def test_strided_buffers_and_zero_batch():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("dtype,ways", [("f64", 0), ("f64", 2), ("f64", 4),
-                                        ("f32", 0), ("f32", 2), ("f32", 4), ("f32", 8)])
-def test_random_20k_program_full_batch_sampled(dtype, ways):
-    """The 20,000-op workload at N = 65536 in each launch configuration the
-    bench chooses from (one thread per instance, or 2, 4 or (FP32) 8 warps per
-    group of 32 instances); 256 sampled instances (and the ragged tail) are
-    checked against the oracle."""
+@pytest.mark.parametrize("dtype,launch", [
+    ("f64", dict(ways=0)), ("f64", dict(ways=2)), ("f64", dict(ways=4)),
+    ("f64", dict(ways=4, coop_groups=2)), ("f64", dict(ways=0, maxrregcount=128)),
+    ("f32", dict(ways=0)), ("f32", dict(ways=2)), ("f32", dict(ways=4)), ("f32", dict(ways=8)),
+    ("f32", dict(ways=0, maxrregcount=128)), ("f32", dict(ways=0, maxrregcount=128, pair_calls=256)),
+    ("f32", dict(ways=0, inst_per_thread=2))], ids=lambda v: str(v))
+def test_random_20k_program_full_batch_sampled(dtype, launch):
+    """The 20,000-op workload at N = 65536 in the launch configurations the
+    bench's autotuner chooses from (one thread per instance, with register
+    caps, paired math calls or two instances per thread; or 2, 4, 8 warps per
+    group of 32 instances, 1 or 2 groups per CTA), including the ones it
+    picks on GB300 (FP64: 4 warps, 2 groups; FP32: 128-register cap with
+    paired calls); 256 sampled instances (and the ragged tail) are checked
+    against the oracle."""
     ir = programs.random_program(20000, seed=0).to_bytes()
     N = 65536
     x = inputs.normal(64, N, seed=1)
-    fn = Function(ir, dtype=dtype, ways=ways)
+    fn = Function(ir, dtype=dtype, **launch)
     if dtype == "f32":
         x = x.astype(np.float32).astype(np.float64)
     y = run(fn, x)
