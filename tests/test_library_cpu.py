@@ -44,9 +44,19 @@ def test_binding_constants_match_the_header():
 
 
 def test_default_options():
+    """The defaults the header states, read through the binding's struct: a
+    field out of step with include/cusadi.h would show up as a wrong value."""
     o = L.cusadi_default_options()
     assert (o.dtype, o.path, o.block, o.fmad, o.schedule) == (0, 0, 128, 1, 1)
+    assert (o.compile_limit_ops, o.segment_ops, o.maxrregcount, o.inline_math) == (300000, 40000, 0, 0)
     assert (o.ways, o.own_math, o.debug_checks, o.adjoint) == (0, 0, 0, 0)
+    assert (o.inst_per_thread, o.coop_groups, o.sync_every, o.interp_shared_kb) == (1, 1, 0, 48)
+    assert (o.spill_values, o.spill_shared_kb, o.pair_calls) == (0, 96, 0)
+    assert o.cache_dir is None
+    src = open(os.path.join(ROOT, "include", "cusadi.h")).read()
+    body = src[src.index("typedef struct {\n  int32_t dtype;"):src.index("} cusadi_options;")]
+    fields = re.findall(r"^\s*(?:int32_t|int64_t|const char\*)\s+(\w+);", body, flags=re.M)
+    assert fields == [f for f, _ in L.cusadi_options._fields_]
 
 
 def test_debug_checks_instrument_the_stores():
