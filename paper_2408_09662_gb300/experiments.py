@@ -46,11 +46,21 @@ def _spd(n, N, seed=0):
     return np.vstack([A[:, il[0], il[1]].T, rng.standard_normal((n, N))])
 
 
-def _gpu_ms(f, reps=5):
+_FLUSH = []
+
+
+def _gpu_ms(f, reps=5, flush=False):
+    """Median CUDA-event time of f() in ms.  flush=True writes 256 MB (twice the
+    L2) before every timed launch, so a multi-megabyte kernel's code and its
+    inputs come from DRAM as they do between unrelated launches."""
     f()
     torch.cuda.synchronize()
+    if flush and not _FLUSH:
+        _FLUSH.append(torch.empty(256 << 20, dtype=torch.uint8, device="cuda"))
     ts = []
     for _ in range(reps):
+        if flush:
+            _FLUSH[0].zero_()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
         f()
@@ -257,7 +267,8 @@ def batch_sweep(ways_list=(4, 8, 16), reps=7):
     """The uneven batch (8 random programs of the 20k-op generator, seeds
     100..107, FP32) with its long few-instance programs as satellite kernels
     of W warps per group: persistent graph launch at each tile size, the 8
-    plain launches, and each satellite-sized program alone at each W."""
+    plain launches, and each satellite-sized program alone at each W; L2
+    flushed before every timed launch."""
     irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(UNEVEN_BATCH)]
     xs = [torch.tensor(inputs.normal(64, N, seed=200 + j), dtype=torch.float32, device="cuda")
           for j, (_, N) in enumerate(UNEVEN_BATCH)]
@@ -273,8 +284,8 @@ def batch_sweep(ways_list=(4, 8, 16), reps=7):
         per = []
         for blk in (32, 64, 128):
             b.set_block(blk)
-            per.append(_gpu_ms(lambda: b(xs, outs), reps=reps))
-        plain = _gpu_ms(lambda: b(xs, outs, mode="plain"), reps=reps)
+            per.append(_gpu_ms(lambda: b(xs, outs), reps=reps, flush=True))
+        plain = _gpu_ms(lambda: b(xs, outs, mode="plain"), reps=reps, flush=True)
         rows.append((w, setup, per, plain))
         print(f"| {w} | {setup:.0f} | {per[0]:.3f} / {per[1]:.3f} / {per[2]:.3f} | {plain:.3f} |", flush=True)
     print("\n| program | N | ways | ms alone |")
@@ -284,9 +295,22 @@ def batch_sweep(ways_list=(4, 8, 16), reps=7):
         for w in (0,) + tuple(ways_list):
             fn = Function(irs[j], dtype="f32", ways=w)
             y = torch.empty((32, N), dtype=torch.float32, device="cuda")
-            ms = _gpu_ms(lambda: fn(xs[j], out=y), reps=reps)
+            ms = _gpu_ms(lambda: fn(xs[j], out=y), reps=reps, flush=True)
             rows.append((n, N, w, ms))
             print(f"| random {n // 1000}k ops | {N} | {w} | {ms:.3f} |", flush=True)
+    # what sets the batch's length: subsets of the programs at 4 warps per group
+    print("\n| what runs (ways 4, best tile of 32/64/128) | ms |")
+    print("|---|---|")
+    for name, sel in (("all 8", range(8)), ("without the 200k-op program", range(7)),
+                      ("without the 200k- and 150k-op programs", range(6)),
+                      ("the four satellites only", range(4, 8)), ("the four scheduler programs only", range(4)),
+                      ("the 200k-op program alone", [7])):
+        sel = list(sel)
+        b = Batch([irs[j] for j in sel], [UNEVEN_BATCH[j][1] for j in sel], dtype="f32", ways=4)
+        X, O = [xs[j] for j in sel], [outs[j] for j in sel]
+        best = min(_gpu_ms(lambda: (b.set_block(blk), b(X, O))[1], reps=reps, flush=True) for blk in (32, 64, 128))
+        rows.append((name, best))
+        print(f"| {name} | {best:.3f} |", flush=True)
     return rows
 
 
