@@ -451,6 +451,8 @@ def run_experiment(name):
         experiments.interp_sweep()
     elif name == "spill":
         experiments.spill_sweep()
+    elif name == "tune":
+        experiments.tune_sweep()
     else:
         from oracle import Oracle
         cores = os.cpu_count() or 1
@@ -489,7 +491,7 @@ def main():
                          '"coop_groups": 2}\'): no tuning')
     ap.add_argument("--launch32", default=None,
                     help="fixed launch options of the FP32 kernel as JSON: no tuning")
-    ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc", "roa", "batch", "interp", "spill"],
+    ap.add_argument("--experiment", choices=["ldlt", "coop", "mpc", "roa", "batch", "interp", "spill", "tune"],
                     help="run one of the paper's experiments instead (markdown table, no JSON line); "
                          "ldlt adds the CPU oracle as its CPU baseline column")
     args = ap.parse_args()

@@ -369,6 +369,48 @@ def spill_sweep(reps=7):
     return rows
 
 
+def tune_sweep(reps=5, ways=(0, 2, 4, 8)):
+    """The autotuner (tune.autotune: L2 flushed before every timed launch,
+    median of `reps`) on the kernels the default launch leaves furthest from
+    their roofline: the SRB step's forward and reverse sweep at N = 65,536
+    (gain rows broadcast, their adjoints reduced over instances) and the
+    closed-form MPC at N = 16,384 in FP64 and mixed precision.  The default
+    launch (one thread per instance) is the tuner's ways = 0 candidate."""
+    from .tune import autotune
+    rng = np.random.default_rng(0)
+    Kn = rng.normal(0, 0.1, (144, 1))
+    Nk, Nm = 65536, 16384
+    rk = np.random.default_rng(1)
+    Xs = np.vstack([np.tile(Kn, (1, Nk)), rk.uniform(-0.1, 0.1, (12, Nk)), np.zeros((1, Nk))])
+    rm = np.random.default_rng(0)
+    Xm = np.vstack([rm.uniform(-0.5, 0.5, (6, Nm)), rm.uniform(-1, 1, (2, Nm))])
+    srb, mpc = programs.srb_step(), programs.quadrotor_mpc()
+    cases = [("SRB step forward", srb, "f32", Xs, False), ("SRB step reverse sweep", srb, "f32", Xs, True),
+             ("SRB step reverse sweep", srb, "f64", Xs, True),
+             ("quadrotor MPC", mpc, "f64", Xm, False), ("quadrotor MPC", mpc, "mixed", Xm, False)]
+    tdt = {"f64": torch.float64, "f32": torch.float32, "mixed": torch.float32}
+    print("| kernel | dtype | N | default ms | tuned ms | speedup | chosen launch | candidates | tuning s |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    rows = []
+    for name, prog, dt, X, adj in cases:
+        Xd = X if dt == "f64" else X.astype(np.float32).astype(np.float64)
+        x = torch.tensor(Xd, dtype=tdt[dt], device="cuda")
+        kw = {}
+        if adj:
+            kw = dict(ybar=torch.ones((prog.nnz_out, X.shape[1]), dtype=tdt[dt], device="cuda"),
+                      adjoint_kw=dict(reduce_broadcast=True))
+        t0 = time.perf_counter()
+        fn = autotune(prog.to_bytes(), x, dt, ways=ways, reps=reps, use_cache=False, **kw)
+        secs = time.perf_counter() - t0
+        rec = fn.tune_record
+        base = next(ms for o, ms in rec["candidates"] if o == {"ways": 0})
+        opts = ", ".join(f"{k}={v}" for k, v in sorted(rec["options"].items()))
+        rows.append((name, dt, X.shape[1], base, rec["ms"], rec["options"]))
+        print(f"| {name} | {dt} | {X.shape[1]} | {base:.4f} | {rec['ms']:.4f} | {base / rec['ms']:.2f}x | "
+              f"{opts} | {len(rec['candidates'])} | {secs:.0f} |", flush=True)
+    return rows
+
+
 def one_kernel(program="random20k", dtype="f64", N=4096, ways=0, reps=3, adjoint=False):
     """Compile one program and launch it `reps` times (a small case for a
     profiler); adjoint: its reverse sweep (broadcast rows reduced) instead."""
@@ -410,6 +452,8 @@ def main(argv):
         interp_sweep()
     elif which == "spill":
         spill_sweep()
+    elif which == "tune":
+        tune_sweep()
     elif which == "one":
         # one <program> <dtype> <N> <ways> [adjoint]
         prog, dt, N, w = (argv[2:] + ["random20k", "f64", "4096", "0"][len(argv) - 2:])[:4]

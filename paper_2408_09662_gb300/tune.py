@@ -55,12 +55,13 @@ def _refinements(best: dict, dtype: str, n_ops: int, n_slots: int) -> list:
     return out
 
 
-def _key(ir: bytes, dtype: str, N: int, fixed: dict, device) -> str:
+def _key(ir: bytes, dtype: str, N: int, fixed: dict, device, target: str = "eval") -> str:
     props = torch.cuda.get_device_properties(device)
     bucket = 1 << max(0, (int(N) - 1).bit_length())
     h = hashlib.sha256(ir).hexdigest()[:20]
     fx = ",".join(f"{k}={fixed[k]}" for k in sorted(fixed))
-    return f"{h}|{props.name}|sm_{props.major}{props.minor}|{dtype}|N<={bucket}|{fx}"
+    key = f"{h}|{props.name}|sm_{props.major}{props.minor}|{dtype}|N<={bucket}|{fx}"
+    return key if target == "eval" else key + "|" + target
 
 
 def _load_cache(path: str) -> dict:
@@ -81,16 +82,16 @@ def _store_cache(path: str, key: str, rec: dict) -> None:
     os.replace(tmp, path)
 
 
-def _time(fn: Function, x: torch.Tensor, y: torch.Tensor, flush: torch.Tensor, reps: int) -> float:
+def _time(run, flush: torch.Tensor, reps: int, device) -> float:
     for _ in range(2):
-        fn(x, out=y)
+        run()
     ts = []
-    stream = torch.cuda.current_stream(x.device)
+    stream = torch.cuda.current_stream(device)
     for _ in range(reps):
         flush.zero_()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        fn(x, out=y)
+        run()
         e.record(stream)
         e.synchronize()
         ts.append(s.elapsed_time(e))
@@ -99,15 +100,22 @@ def _time(fn: Function, x: torch.Tensor, y: torch.Tensor, flush: torch.Tensor, r
 
 def autotune(program, x: torch.Tensor, dtype: str = "f64", ways=(0, 2, 4, 8), refine: bool = True,
              reps: int = 5, flush_bytes: int = 256 << 20, cache_dir=DEFAULT_CACHE,
-             use_cache: bool = True, compile_workers: int = 8, **fixed) -> Function:
+             use_cache: bool = True, compile_workers: int = 8, ybar: torch.Tensor | None = None,
+             adjoint_kw: dict | None = None, **fixed) -> Function:
     """The program compiled in the fastest configuration found for the batch x
     ([nnz_in, N] CUDA tensor of the dtype's element type).  `fixed` options
-    (e.g. fmad=0) apply to every candidate.  The returned Function carries
-    `.tune_record`: the chosen options, their time and every candidate's time
-    (ms), and whether the record came from the cache."""
+    (e.g. fmad=0) apply to every candidate.  With `ybar` ([nnz_out, N]) the
+    candidates are timed on the reverse sweep, `fn.adjoint(x, ybar, **adjoint_kw)`,
+    instead of the forward evaluation (the launch options apply to both kernels
+    of a Function; the cache keeps the two choices apart).  The returned Function
+    carries `.tune_record`: the chosen options, their time and every candidate's
+    time (ms), what was timed, and whether the record came from the cache."""
     ir = _program_bytes(program)
     N = int(x.shape[1])
-    key = _key(ir, dtype, N, fixed, x.device)
+    adjoint_kw = dict(adjoint_kw or {})
+    target = "eval" if ybar is None else \
+        "adjoint(" + ",".join(f"{k}={adjoint_kw[k]}" for k in sorted(adjoint_kw)) + ")"
+    key = _key(ir, dtype, N, fixed, x.device, target)
     path = os.path.join(cache_dir, "tuning.json") if cache_dir else None
     if use_cache and path:
         rec = _load_cache(path).get(key)
@@ -126,8 +134,13 @@ def autotune(program, x: torch.Tensor, dtype: str = "f64", ways=(0, 2, 4, 8), re
         with ThreadPoolExecutor(max(1, min(compile_workers, len(cands)))) as ex:
             fns = list(ex.map(build, cands))
         for c, fn in zip(cands, fns):       # timed one after the other, nothing else on the GPU
-            y = torch.empty((fn.nnz_out, N), dtype=fn.torch_dtype, device=x.device)
-            tried[tuple(sorted(c.items()))] = (_time(fn, x, y, flush, reps), fn)
+            if ybar is None:
+                y = torch.empty((fn.nnz_out, N), dtype=fn.torch_dtype, device=x.device)
+                run = lambda: fn(x, out=y)
+            else:
+                y = torch.empty((fn.nnz_in, N), dtype=fn.torch_dtype, device=x.device)
+                run = lambda: fn.adjoint(x, ybar, out=y, **adjoint_kw)
+            tried[tuple(sorted(c.items()))] = (_time(run, flush, reps, x.device), fn)
 
     run_round([{"ways": int(w)} for w in ways])
     if refine:
@@ -149,7 +162,7 @@ def autotune(program, x: torch.Tensor, dtype: str = "f64", ways=(0, 2, 4, 8), re
             run_round([dict(dict(best), pair_calls=256)])
     best = min(tried, key=lambda k: tried[k][0])
     ms, fn = tried[best]
-    rec = {"options": dict(best), "ms": ms, "N": N,
+    rec = {"options": dict(best), "ms": ms, "N": N, "target": target,
            "candidates": [[dict(k), v[0]] for k, v in sorted(tried.items(), key=lambda kv: kv[1][0])]}
     if path:
         _store_cache(path, key, rec)

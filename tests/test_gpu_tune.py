@@ -44,3 +44,28 @@ def test_autotune_keeps_the_fastest_and_caches_it(tmp_path):
     # another batch size bucket or fixed option is another entry
     autotune(ir, x[:, :1000].contiguous(), "f64", ways=(0,), refine=False, cache_dir=str(tmp_path), fmad=0)
     assert len(json.load(open(os.path.join(str(tmp_path), "tuning.json")))) == 2
+
+
+def test_autotune_on_the_reverse_sweep(tmp_path):
+    """With ybar the candidates are timed on the adjoint; the chosen Function's
+    reverse sweep matches the oracle's, and the record is kept apart from the
+    forward choice of the same program."""
+    ir = programs.srb_step().to_bytes()
+    rng = np.random.default_rng(73)
+    N = 2051
+    X = np.vstack([np.tile(rng.normal(0, 0.1, (144, 1)), (1, N)), rng.uniform(-0.1, 0.1, (12, N)),
+                   np.zeros((1, N))])
+    ybar = rng.standard_normal((13, N))
+    x, yb = torch.tensor(X, device="cuda"), torch.tensor(ybar, device="cuda")
+    fn = autotune(ir, x, "f64", ways=(0, 4), cache_dir=str(tmp_path), reps=3, ybar=yb,
+                  adjoint_kw=dict(reduce_broadcast=True))
+    rec = fn.tune_record
+    assert rec["target"] == "adjoint(reduce_broadcast=True)" and rec["ms"] == min(t for _, t in rec["candidates"])
+    got = fn.adjoint(x, yb, reduce_broadcast=True).cpu().numpy()
+    ref = Oracle(ir).adjoint(X, ybar)
+    np.testing.assert_allclose(got[144:], ref[144:], rtol=0, atol=1e-12 * np.max(np.abs(ref[144:])))
+    red = ref[:144].sum(axis=1)
+    np.testing.assert_allclose(got[:144, 0], red, rtol=1e-11, atol=1e-12 * np.max(np.abs(red)))
+    fwd = autotune(ir, x, "f64", ways=(0,), refine=False, cache_dir=str(tmp_path), reps=3)
+    assert fwd.tune_record["target"] == "eval"
+    assert len(json.load(open(os.path.join(str(tmp_path), "tuning.json")))) == 2
