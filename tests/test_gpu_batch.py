@@ -147,7 +147,7 @@ def test_uneven_batch_at_stated_sizes_against_the_oracle():
     oracle under the FP32 rule max(2e-4 s_k, 2 B32_k,i, 4 S_k): B32 is the
     first-order rounding bound, S_k the largest deviation of 8 Monte Carlo
     arithmetic runs at FP32 sizes on output row k.  Past ~20k ops most outputs
-    keep no correct float digit (S_k reaches s_k), so only S_k can judge them;
+    keep no correct float digit (S_k reaches s_k), so only S_k can bound their error;
     the fraction of outputs within the plain 2e-4 s_k is recorded and must
     fall with depth as the oracle says it does."""
     irs = [programs.random_program(n, seed=100 + j).to_bytes() for j, (n, _) in enumerate(C5_SIZES)]
