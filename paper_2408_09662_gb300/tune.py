@@ -39,17 +39,20 @@ import torch
 from .api import DEFAULT_CACHE, Function, _program_bytes
 
 
-def _refinements(best: dict, dtype: str, n_ops: int, n_slots: int) -> list:
+def _refinements(best: dict, dtype: str, n_ops: int, n_slots: int, adjoint: bool = False) -> list:
     """Candidate option sets one step away from `best`.  Instances per thread
     multiply the live values a thread holds, so a count needing more than
     twice the 255 registers a thread can have (two per FP64 value) is not
-    tried: the spills would dominate."""
+    tried: the spills would dominate.  n_slots is the forward program's live
+    set; a reverse sweep holds at least those values and their adjoints, so for
+    it the estimate is doubled."""
     out = []
     if best.get("ways", 0) == 0:
         regs_per_value = 2 if dtype == "f64" else 1
-        out += [dict(best, inst_per_thread=r) for r in (2, 4) if n_slots * r * regs_per_value <= 512]
+        live = n_slots * (2 if adjoint else 1)
+        out += [dict(best, inst_per_thread=r) for r in (2, 4) if live * r * regs_per_value <= 512]
         # register caps: more resident warps at the price of some spills
-        out += [dict(best, maxrregcount=r) for r in (128, 96, 64) if n_slots * regs_per_value > r]
+        out += [dict(best, maxrregcount=r) for r in (128, 96, 64) if live * regs_per_value > r]
     else:
         out += [dict(best, coop_groups=2), dict(best, coop_groups=4)]
     return out
@@ -153,7 +156,7 @@ def autotune(program, x: torch.Tensor, dtype: str = "f64", ways=(0, 2, 4, 8), re
             if keys:
                 best = min(keys, key=lambda k: tried[k][0])
                 info = tried[best][1].info
-                cands += _refinements(dict(best), dtype, info.n_ops, info.n_slots)
+                cands += _refinements(dict(best), dtype, info.n_ops, info.n_slots, adjoint=ybar is not None)
         run_round(cands)
         # a one-thread winner also tries paired math calls (sin/cos/exp issued two
         # at a time; measured 4 % on the random 20k-op FP32 kernel)
