@@ -7,6 +7,15 @@
 // all instance-fastest so a warp touches 32 consecutive elements per row.
 // Programs longer than segment_ops are split into several kernels that pass
 // the values live across a cut through a workspace (same SoA layout).
+//
+// Launch shapes of the one-thread form: R consecutive instances per thread
+// (every statement repeated per lane, rows moved as float2/float4/double2
+// when the buffers allow), a register cap through the launch bounds, CTA
+// barriers every few hundred ops, a register budget that moves the values
+// past it to shared-memory slots, workspace rows or re-reads, and pairs of
+// out-of-line math calls of the same function issued as one two-argument
+// call.  The cooperative form (W warps per 32 instances, its schedule from
+// plan_coop in coop.cpp) is generate_coop, further down.
 #include <algorithm>
 #include <cinttypes>
 #include <cmath>
